@@ -1,0 +1,173 @@
+/*
+ * pma.h - C ABI of the GB300 Voronoi particle-merging library.
+ *
+ * The library implements the per-cell recursive phase-space partition and
+ * merge of Luu, Tueckmantel & Pukhov, "Voronoi particle merging algorithm for
+ * PIC codes" (arXiv:1504.00636), Sec. 3 "Algorithm", Steps 1-7:
+ *   - Input (Sec. 3): per-particle weight w, position x (dx components) and
+ *     momentum p (dp components), tolerances T_X, T_P and N_min; a cell is
+ *     merged only when it holds more than N_min particles.
+ *   - Step 1: the particles of each simulation cell form the first set V0.
+ *   - Step 2: weighted centroid and standard deviation per axis; CVs
+ *     Delta_x = sigma/L (Eq. cv_x, L = grid-cell size on that axis) and
+ *     Delta_p = sigma/|P| (Eq. cv_p).
+ *   - Step 3: a set is final when every Delta is <= its tolerance.
+ *   - Step 4 (Eq. step_4): otherwise the axis k with the largest Delta is cut.
+ *   - Step 5: V1 = {q_k <= Q_k}, V2 = {q_k > Q_k}.
+ *   - Step 6: recurse on V1 and V2.
+ *   - Step 7: every final set is replaced by its centroid (W, X, P); a
+ *     one-particle set is kept as it is.
+ * Output order is canonical: cells ascending, and within a cell the final
+ * sets in V1-before-V2 depth-first order.
+ *
+ * All pointers named "device" are CUDA device pointers (or managed memory)
+ * of the current device; "host" pointers are ordinary host memory.  Arrays
+ * are structure-of-arrays: pos[a] is the a-th position component of all n
+ * particles.  Every function returns a status code (PMA_OK = 0).
+ * A handle is not thread-safe: use one handle per host thread / stream.
+ */
+#ifndef PMA_H
+#define PMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define PMA_OK 0
+#define PMA_ERR_INVALID_ARG 1 /* null pointer, bad size, tol < 0 or non-finite */
+#define PMA_ERR_INPUT 2       /* particle data: cell id out of range, w <= 0,
+                                 non-finite w / x / p (found on the device) */
+#define PMA_ERR_CUDA 3        /* a CUDA runtime call failed; see pma_last_error */
+#define PMA_ERR_NOMEM 4       /* device or host allocation failed */
+#define PMA_ERR_CAPACITY 5    /* n larger than the handle's capacity */
+#define PMA_ERR_TIMEOUT 6     /* a bounded device wait gave up (no hang) */
+#define PMA_ERR_INTERNAL 7    /* an internal bound was exceeded (reported, not trapped) */
+
+/* ---- precision ------------------------------------------------------- */
+#define PMA_FP64 0  /* FP64 storage, plain FP64 sums and decisions */
+#define PMA_MIXED 1 /* FP32 storage of x, p, w; compensated FP32 moment sums;
+                       FP64 split decision and FP64 merged W and P */
+
+/* ---- config flags ---------------------------------------------------- */
+#define PMA_FLAG_NO_INDEX 1u  /* do not accept an output index (saves 4 B/particle) */
+
+typedef struct pma_handle pma_handle;
+
+typedef struct pma_config {
+    int32_t dx;           /* position components, 1..3 */
+    int32_t dp;           /* momentum components, 1..3 */
+    double cell_size[3];  /* L per position axis (Eq. cv_x), > 0 */
+    int64_t n_cells;      /* cell ids lie in [0, n_cells); >= 1 */
+    int32_t n_min;        /* a cell is merged only if it holds > n_min particles */
+    int32_t precision;    /* PMA_FP64 or PMA_MIXED */
+    int64_t capacity;     /* largest n of any call; sizes the workspace; <= 2^31-1 */
+    uint32_t flags;       /* PMA_FLAG_* */
+} pma_config;
+
+/*
+ * Caller-owned device output buffers; every array has room for `capacity`
+ * entries (the output count M never exceeds the input count n).
+ *   cell[M]           int32 cell id of each merged particle
+ *   pos[a][M]         FP64 (PMA_FP64) or FP32 (PMA_MIXED) centroid position
+ *   mom[a][M]         FP64 centroid momentum
+ *   w[M]              FP64 centroid weight
+ *   index[n]          int32: output slot of every input particle, or NULL
+ *   count_dev         int64 device word receiving M, or NULL
+ */
+typedef struct pma_output {
+    int32_t *cell;
+    void *pos[3];
+    double *mom[3];
+    double *w;
+    int32_t *index;
+    int64_t *count_dev;
+} pma_output;
+
+/* Per-call counters (filled after a synchronous call). */
+typedef struct pma_stats {
+    int64_t n_in;              /* particles in */
+    int64_t n_out;             /* merged particles out (M) */
+    int64_t cells_merged;      /* cells with more than max(n_min, 1) particles */
+    int64_t cells_passthrough; /* cells copied verbatim (1..n_min particles) */
+    int64_t splits;            /* Step 4-6 cuts taken */
+    int64_t leaves;            /* final sets (Step 7) in merged cells */
+    int64_t depth_sum;         /* sum over particles of their final set's depth */
+    int64_t degenerate_cuts;   /* cuts whose rounded centroid left a side empty */
+    int64_t big_cells;         /* cells too large for one CTA's shared memory */
+    int64_t sorted_input;      /* 1 if the cell ids were already non-decreasing */
+} pma_stats;
+
+/*
+ * Create a handle: validates cfg, selects the device current at the call,
+ * and allocates the device workspace for `capacity` particles.  *out is set
+ * on success and untouched on failure.
+ */
+int pma_create(const pma_config *cfg, pma_handle **out);
+
+/*
+ * Merge n particles (Sec. 3, Steps 1-7) on `stream` (a cudaStream_t; 0 =
+ * legacy default stream).
+ *   cells[n]      device int32 cell id of each particle, in [0, n_cells)
+ *   pos[a][n]     device positions, a < dx (FP64 for PMA_FP64, FP32 for PMA_MIXED)
+ *   mom[a][n]     device momenta, a < dp (same type)
+ *   weights[n]    device weights w > 0 (same type)
+ *   tol_x, tol_p  the tolerances T_X, T_P of Step 3, finite and >= 0
+ *   out           caller-owned device output buffers (see pma_output)
+ *   count_host    host int64 receiving M, or NULL
+ * Inputs are never modified.  When count_host is non-NULL the call waits
+ * for the stream and returns the status of the device work (PMA_ERR_INPUT
+ * for bad particle data); when it is NULL the call only enqueues work and
+ * the device status is read by pma_sync().
+ */
+int pma_merge(pma_handle *h, int64_t n, const int32_t *cells,
+              const void *const *pos, const void *const *mom,
+              const void *weights, double tol_x, double tol_p,
+              const pma_output *out, int64_t *count_host, void *stream);
+
+/*
+ * Same as pma_merge with HOST input and output arrays (types as above; the
+ * output arrays are host arrays of `capacity` entries).  The handle stages
+ * the data through its own device buffers (allocated on first use) and
+ * always waits for completion.
+ */
+int pma_merge_host(pma_handle *h, int64_t n, const int32_t *cells,
+                   const void *const *pos, const void *const *mom,
+                   const void *weights, double tol_x, double tol_p,
+                   const pma_output *out_host, int64_t *count_host, void *stream);
+
+/* Wait for the handle's last enqueued call and return its device status. */
+int pma_sync(pma_handle *h);
+
+/* Counters of the last completed call. */
+int pma_get_stats(const pma_handle *h, pma_stats *out);
+
+/*
+ * Per-stage device timing.  When enabled, every pma_merge records CUDA
+ * events on its stream between the stages; pma_get_timing (after the call
+ * completed) writes up to n durations in milliseconds, averaged over the
+ * calls since timing was enabled (the last 64 of them):
+ *   [0] Step 1 binning   [1] big-cell cuts   [2] per-cell partition
+ *   [3] big-cell pieces  [4] Step 7 emit     [5] whole call
+ * and returns PMA_ERR_INVALID_ARG when timing is off or nothing was timed.
+ */
+#define PMA_N_STAGES 6
+int pma_set_timing(pma_handle *h, int enable);
+int pma_get_timing(const pma_handle *h, float *ms, int n);
+
+/* Release the handle and its device memory (NULL is accepted). */
+int pma_destroy(pma_handle *h);
+
+/* Static description of a status code. */
+const char *pma_error_string(int code);
+
+/* Text of the last error on this handle ("" if none). */
+const char *pma_last_error(const pma_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMA_H */

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of the C ABI in ``include/pma.h``.
+
+Functions carry the C names (``pma_create``, ``pma_merge``, ...) and only
+marshal arguments: device arrays are torch CUDA tensors whose ``data_ptr()``
+is handed to the library, host arrays are numpy arrays or pinned CPU tensors.
+Every step of the merge runs in the CUDA library; there is no other code
+path, and loading fails loudly when the library cannot be found or built.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+from . import _build
+
+PMA_OK = 0
+PMA_ERR_INVALID_ARG = 1
+PMA_ERR_INPUT = 2
+PMA_ERR_CUDA = 3
+PMA_ERR_NOMEM = 4
+PMA_ERR_CAPACITY = 5
+PMA_ERR_TIMEOUT = 6
+PMA_ERR_INTERNAL = 7
+
+PMA_FP64 = 0
+PMA_MIXED = 1
+PMA_FLAG_NO_INDEX = 1
+
+SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
+           "pma_set_timing", "pma_get_timing", "pma_destroy", "pma_error_string",
+           "pma_last_error")
+PMA_N_STAGES = 6
+STAGES = ("binning", "big_cells", "cells", "pieces", "emit", "total")
+
+
+class pma_config(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_int32), ("dp", ctypes.c_int32),
+                ("cell_size", ctypes.c_double * 3), ("n_cells", ctypes.c_int64),
+                ("n_min", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("capacity", ctypes.c_int64), ("flags", ctypes.c_uint32)]
+
+
+class pma_output(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_void_p), ("pos", ctypes.c_void_p * 3),
+                ("mom", ctypes.c_void_p * 3), ("w", ctypes.c_void_p),
+                ("index", ctypes.c_void_p), ("count_dev", ctypes.c_void_p)]
+
+
+class pma_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "n_in", "n_out", "cells_merged", "cells_passthrough", "splits", "leaves",
+        "depth_sum", "degenerate_cuts", "big_cells", "sorted_input")]
+
+
+class PmaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pma status %d (%s): %s" % (code, pma_error_string(code), msg))
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``libpma.so`` (building it with nvcc when absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libpma.so not found at %s; run __graft_entry__.build()" % path)
+            lib = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            lib.pma_create.argtypes = [ctypes.POINTER(pma_config), ctypes.POINTER(P)]
+            lib.pma_create.restype = ctypes.c_int
+            args = [P, ctypes.c_int64, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                    ctypes.POINTER(pma_output), ctypes.POINTER(ctypes.c_int64), P]
+            lib.pma_merge.argtypes = args
+            lib.pma_merge.restype = ctypes.c_int
+            lib.pma_merge_host.argtypes = args
+            lib.pma_merge_host.restype = ctypes.c_int
+            lib.pma_sync.argtypes = [P]
+            lib.pma_sync.restype = ctypes.c_int
+            lib.pma_get_stats.argtypes = [P, ctypes.POINTER(pma_stats)]
+            lib.pma_get_stats.restype = ctypes.c_int
+            lib.pma_set_timing.argtypes = [P, ctypes.c_int]
+            lib.pma_set_timing.restype = ctypes.c_int
+            lib.pma_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+            lib.pma_get_timing.restype = ctypes.c_int
+            lib.pma_destroy.argtypes = [P]
+            lib.pma_destroy.restype = ctypes.c_int
+            lib.pma_error_string.argtypes = [ctypes.c_int]
+            lib.pma_error_string.restype = ctypes.c_char_p
+            lib.pma_last_error.argtypes = [P]
+            lib.pma_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def pma_error_string(code: int) -> str:
+    return load().pma_error_string(code).decode()
+
+
+def pma_last_error(handle) -> str:
+    return load().pma_last_error(handle).decode()
+
+
+def _check(rc, handle=None):
+    if rc != PMA_OK:
+        raise PmaError(rc, pma_last_error(handle) if handle else "")
+
+
+def pma_create(cfg: pma_config):
+    h = ctypes.c_void_p()
+    _check(load().pma_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def pma_destroy(handle) -> None:
+    _check(load().pma_destroy(handle))
+
+
+def _ptrs(arrs, n=3):
+    out = (ctypes.c_void_p * n)()
+    for i, a in enumerate(arrs):
+        out[i] = a
+    return out
+
+
+def pma_merge(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_output,
+              count_host=True, stream=0):
+    """Raw call: every array argument is a device pointer (int)."""
+    cnt = ctypes.c_int64(-1)
+    rc = load().pma_merge(handle, n, cells, _ptrs(pos), _ptrs(mom), weights, tol_x, tol_p,
+                          ctypes.byref(out), ctypes.byref(cnt) if count_host else None, stream)
+    _check(rc, handle)
+    return cnt.value
+
+
+def pma_merge_host(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_output,
+                   stream=0):
+    """Raw call: every array argument is a host pointer (int)."""
+    cnt = ctypes.c_int64(-1)
+    rc = load().pma_merge_host(handle, n, cells, _ptrs(pos), _ptrs(mom), weights, tol_x, tol_p,
+                               ctypes.byref(out), ctypes.byref(cnt), stream)
+    _check(rc, handle)
+    return cnt.value
+
+
+def pma_sync(handle) -> None:
+    _check(load().pma_sync(handle), handle)
+
+
+def pma_get_stats(handle) -> dict:
+    s = pma_stats()
+    _check(load().pma_get_stats(handle, ctypes.byref(s)), handle)
+    return {k: getattr(s, k) for k, _ in pma_stats._fields_}
+
+
+def pma_set_timing(handle, enable: bool) -> None:
+    _check(load().pma_set_timing(handle, 1 if enable else 0), handle)
+
+
+def pma_get_timing(handle) -> dict:
+    ms = (ctypes.c_float * PMA_N_STAGES)()
+    _check(load().pma_get_timing(handle, ms, PMA_N_STAGES), handle)
+    return dict(zip(STAGES, [float(x) for x in ms]))
+
+
+# ---------------------------------------------------------------- helpers
+
+@dataclasses.dataclass
+class Output:
+    """Device output buffers (torch tensors of `capacity` entries)."""
+    cell: "object"
+    pos: list
+    mom: list
+    w: "object"
+    index: "object"
+    count_dev: "object"
+
+    def struct(self) -> pma_output:
+        o = pma_output()
+        o.cell = self.cell.data_ptr()
+        for a, t in enumerate(self.pos):
+            o.pos[a] = t.data_ptr()
+        for a, t in enumerate(self.mom):
+            o.mom[a] = t.data_ptr()
+        o.w = self.w.data_ptr()
+        o.index = self.index.data_ptr() if self.index is not None else None
+        o.count_dev = self.count_dev.data_ptr() if self.count_dev is not None else None
+        return o
+
+
+class Merger:
+    """Owns one handle; ``merge`` takes torch CUDA tensors in SoA layout."""
+
+    def __init__(self, dx, dp, n_cells, capacity, cell_size=(1.0, 1.0, 1.0), n_min=0,
+                 precision="fp64", flags=0):
+        import torch
+        self.torch = torch
+        self.dx, self.dp, self.n_cells, self.capacity = dx, dp, int(n_cells), int(capacity)
+        self.mixed = precision == "mixed"
+        cfg = pma_config()
+        cfg.dx, cfg.dp = dx, dp
+        for a in range(3):
+            cfg.cell_size[a] = float(cell_size[a]) if a < len(cell_size) else 1.0
+        cfg.n_cells = int(n_cells)
+        cfg.n_min = int(n_min)
+        cfg.precision = PMA_MIXED if self.mixed else PMA_FP64
+        cfg.capacity = int(capacity)
+        cfg.flags = flags
+        self.handle = pma_create(cfg)
+        self.dtype = torch.float32 if self.mixed else torch.float64
+
+    def close(self):
+        if self.handle is not None:
+            pma_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_output(self, device="cuda", index=True) -> Output:
+        t = self.torch
+        N = max(self.capacity, 1)
+        return Output(t.empty(N, dtype=t.int32, device=device),
+                      [t.empty(N, dtype=self.dtype, device=device) for _ in range(self.dx)],
+                      [t.empty(N, dtype=t.float64, device=device) for _ in range(self.dp)],
+                      t.empty(N, dtype=t.float64, device=device),
+                      t.empty(N, dtype=t.int32, device=device) if index else None,
+                      t.zeros(1, dtype=t.int64, device=device))
+
+    def merge(self, cells, pos, mom, w, tol_x, tol_p, out: Output = None, sync=True,
+              stream=None):
+        """Merge device tensors; returns (M or None, out)."""
+        if out is None:
+            out = self.alloc_output(cells.device)
+        n = int(cells.shape[0])
+        if stream is None:
+            stream = self.torch.cuda.current_stream(cells.device)
+        m = pma_merge(self.handle, n, cells.data_ptr(), [p.data_ptr() for p in pos],
+                      [p.data_ptr() for p in mom], w.data_ptr(), float(tol_x), float(tol_p),
+                      out.struct(), count_host=sync, stream=stream.cuda_stream)
+        return (m if sync else None), out
+
+    def sync(self):
+        pma_sync(self.handle)
+
+    def stats(self) -> dict:
+        return pma_get_stats(self.handle)
+
+    def set_timing(self, enable: bool = True) -> None:
+        pma_set_timing(self.handle, enable)
+
+    def timing(self) -> dict:
+        return pma_get_timing(self.handle)

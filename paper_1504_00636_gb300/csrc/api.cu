@@ -1,0 +1,517 @@
+// C ABI of the library (declared in include/pma.h): handle lifetime, argument
+// checks, the per-call launch sequence and status read-back.
+//
+// One call of pma_merge enqueues, on the caller's stream and without any host
+// synchronisation:
+//   hist / scan / scatter   Step 1: cells -> sorted positions
+//   big_kernel              cells too large for shared memory: top cuts in
+//                           global memory until every piece fits
+//   unit_kernel (cells)     Steps 2-6 per cell in shared memory
+//   unit_kernel (pieces)    Steps 2-6 on the pieces of big cells
+//   emit_kernel             Step 7: centroids, compacted, canonical order
+// and a 1-line status copy (count, error bits, counters) to pinned memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pma.h"
+#include "pma_launch.h"
+
+using namespace pma;
+
+namespace {
+
+struct Ctl {
+  unsigned err;
+  int32_t unsorted;
+  int32_t big_count;
+  int32_t big_next;
+  int32_t piece_count;
+  int32_t unit_next[2];
+  int32_t bin_ticket;
+  int32_t emit_ticket;
+  int32_t pad;
+  int64_t count;
+  unsigned long long stats[kStCount];
+};
+
+constexpr int kRing = 64;  // timed calls kept for pma_get_timing
+
+struct Staging {
+  int32_t *cells = nullptr;
+  void *q[kMaxD] = {};
+  void *w = nullptr;
+  int32_t *out_cell = nullptr;
+  void *out_pos[3] = {};
+  double *out_mom[3] = {};
+  double *out_w = nullptr;
+  int32_t *out_index = nullptr;
+  bool ready = false;
+};
+
+}  // namespace
+
+struct pma_handle {
+  pma_config cfg;
+  int device = 0;
+  int sms = 0;
+  int D = 0;
+  int mixed = 0;
+  int cap = 0;
+  int unit_grid = 0;
+  int64_t capacity = 0;
+  int bin_tiles = 0;
+  int emit_tiles_max = 0;
+  int max_pieces = 0;
+  // workspace
+  int32_t *counts = nullptr, *cell_begin = nullptr, *fill = nullptr;
+  int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
+  uint8_t *head = nullptr;
+  double *rec_w = nullptr, *rec_c = nullptr;
+  unsigned long long *bin_status = nullptr, *emit_status = nullptr;
+  int4 *pieces = nullptr;
+  Ctl *ctl = nullptr;
+  Ctl *ctl_host = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool pending = false;
+  Staging stage;
+  bool timing = false;
+  int timed = 0;     // calls recorded since timing was enabled
+  cudaEvent_t ev[kRing][PMA_N_STAGES] = {};
+  cudaEvent_t *cur_ev = nullptr;
+  std::string last_error;
+  pma_stats stats{};
+};
+
+namespace {
+
+int fail(pma_handle *h, int code, const std::string &msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+int cuda_fail(pma_handle *h, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, PMA_ERR_CUDA, m);
+}
+
+#define PMA_CUDA(h, call)                                     \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_all(pma_handle *h) {
+  void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
+                  h->big_list, h->head, h->rec_w, h->rec_c, h->bin_status, h->emit_status,
+                  h->pieces, h->ctl, h->stage.cells, h->stage.w, h->stage.out_cell,
+                  h->stage.out_w, h->stage.out_index};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int l = 0; l < kMaxD; ++l)
+    if (h->stage.q[l]) cudaFree(h->stage.q[l]);
+  for (int l = 0; l < 3; ++l) {
+    if (h->stage.out_pos[l]) cudaFree(h->stage.out_pos[l]);
+    if (h->stage.out_mom[l]) cudaFree(h->stage.out_mom[l]);
+  }
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  for (auto &row : h->ev)
+    for (auto &e : row)
+      if (e) cudaEventDestroy(e);
+}
+
+// event i of the current call: 0 before binning, 1..4 after each stage,
+// 5 after emit (6 events; stage k spans events k..k+1, the call 0..5)
+void mark(pma_handle *h, int i, cudaStream_t st) {
+  if (h->timing && h->cur_ev) cudaEventRecord(h->cur_ev[i], st);
+}
+
+int status_from_ctl(pma_handle *h) {
+  const Ctl &c = *h->ctl_host;
+  pma_stats &s = h->stats;
+  s.n_out = c.count;
+  s.cells_merged = (int64_t)c.stats[kStCellsMerged];
+  s.cells_passthrough = (int64_t)c.stats[kStCellsPass];
+  s.splits = (int64_t)c.stats[kStSplits];
+  s.leaves = (int64_t)c.stats[kStLeaves];
+  s.depth_sum = (int64_t)c.stats[kStDepth];
+  s.degenerate_cuts = (int64_t)c.stats[kStDegenerate];
+  s.big_cells = (int64_t)c.stats[kStBig];
+  s.sorted_input = c.unsorted ? 0 : 1;
+  if (c.err & kErrInput)
+    return fail(h, PMA_ERR_INPUT,
+                "invalid particle data (cell id out of range, w <= 0 or non-finite value)");
+  if (c.err & kErrTimeout) return fail(h, PMA_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (c.err & kErrInternal)
+    return fail(h, PMA_ERR_INTERNAL, "an internal device bound was exceeded");
+  return PMA_OK;
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *pma_error_string(int code) {
+  switch (code) {
+    case PMA_OK: return "ok";
+    case PMA_ERR_INVALID_ARG: return "invalid argument";
+    case PMA_ERR_INPUT: return "invalid particle data";
+    case PMA_ERR_CUDA: return "CUDA error";
+    case PMA_ERR_NOMEM: return "out of memory";
+    case PMA_ERR_CAPACITY: return "n exceeds the handle capacity";
+    case PMA_ERR_TIMEOUT: return "device wait timed out";
+    case PMA_ERR_INTERNAL: return "internal bound exceeded";
+    default: return "unknown status";
+  }
+}
+
+const char *pma_last_error(const pma_handle *h) { return h ? h->last_error.c_str() : ""; }
+
+int pma_create(const pma_config *cfg, pma_handle **out) {
+  if (!cfg || !out) return PMA_ERR_INVALID_ARG;
+  if (cfg->dx < 1 || cfg->dx > 3 || cfg->dp < 1 || cfg->dp > 3) return PMA_ERR_INVALID_ARG;
+  if (cfg->n_cells < 1 || cfg->n_cells > INT32_MAX - 1) return PMA_ERR_INVALID_ARG;
+  if (cfg->n_min < 0) return PMA_ERR_INVALID_ARG;
+  if (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED) return PMA_ERR_INVALID_ARG;
+  if (cfg->capacity < 0 || cfg->capacity > INT32_MAX) return PMA_ERR_INVALID_ARG;
+  for (int a = 0; a < cfg->dx; ++a)
+    if (!(cfg->cell_size[a] > 0.0) || !std::isfinite(cfg->cell_size[a]))
+      return PMA_ERR_INVALID_ARG;
+  pma_handle *h = new (std::nothrow) pma_handle();
+  if (!h) return PMA_ERR_NOMEM;
+  h->cfg = *cfg;
+  h->D = cfg->dx + cfg->dp;
+  h->mixed = cfg->precision == PMA_MIXED;
+  h->capacity = cfg->capacity;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  int smem_optin = 0;
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return PMA_ERR_CUDA;
+  }
+  // largest unit that fits one CTA's shared memory (static part ~4 KB)
+  int cap = 8192;
+  while (cap > 64 && unit_smem(h->mixed, h->D, cap) + 4096 > (size_t)smem_optin) cap -= 64;
+  h->cap = cap;
+  h->unit_grid = h->sms;
+  const int64_t N = std::max<int64_t>(cfg->capacity, 1);
+  const int64_t C = cfg->n_cells;
+  h->bin_tiles = scan_tiles_for(C);
+  h->emit_tiles_max = emit_tiles_for(N);
+  h->max_pieces = (int)std::min<int64_t>(N, N / 64 + 4096);
+  const int64_t Npad = (N + 15) / 16 * 16;
+  bool ok = dalloc(&h->counts, C) == cudaSuccess && dalloc(&h->cell_begin, C + 1) == cudaSuccess &&
+            dalloc(&h->fill, C) == cudaSuccess && dalloc(&h->perm, N) == cudaSuccess &&
+            dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
+            dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
+            dalloc(&h->rec_w, N) == cudaSuccess &&
+            dalloc(&h->rec_c, (size_t)N * h->D) == cudaSuccess &&
+            dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
+            dalloc(&h->emit_status, h->emit_tiles_max) == cudaSuccess &&
+            dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
+            cudaMallocHost(reinterpret_cast<void **>(&h->ctl_host), sizeof(Ctl)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return PMA_ERR_NOMEM;
+  }
+  memset(h->ctl_host, 0, sizeof(Ctl));
+  *out = h;
+  return PMA_OK;
+}
+
+int pma_destroy(pma_handle *h) {
+  if (!h) return PMA_OK;
+  if (h->pending && h->last_stream) cudaStreamSynchronize(h->last_stream);
+  free_all(h);
+  delete h;
+  return PMA_OK;
+}
+
+static int check_common(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
+                        const void *const *mom, const void *weights, double tol_x,
+                        double tol_p, const pma_output *out) {
+  if (!h) return PMA_ERR_INVALID_ARG;
+  h->last_error.clear();
+  if (n < 0) return fail(h, PMA_ERR_INVALID_ARG, "n < 0");
+  if (n > h->capacity) return fail(h, PMA_ERR_CAPACITY, "n exceeds the handle capacity");
+  if (!finite_nonneg(tol_x) || !finite_nonneg(tol_p))
+    return fail(h, PMA_ERR_INVALID_ARG, "tolerances must be finite and >= 0");
+  if (!out) return fail(h, PMA_ERR_INVALID_ARG, "out is NULL");
+  if (n == 0) return PMA_OK;
+  if (!cells || !pos || !mom || !weights) return fail(h, PMA_ERR_INVALID_ARG, "NULL input");
+  for (int a = 0; a < h->cfg.dx; ++a)
+    if (!pos[a] || !out->pos[a]) return fail(h, PMA_ERR_INVALID_ARG, "NULL position array");
+  for (int a = 0; a < h->cfg.dp; ++a)
+    if (!mom[a] || !out->mom[a]) return fail(h, PMA_ERR_INVALID_ARG, "NULL momentum array");
+  if (!out->cell || !out->w) return fail(h, PMA_ERR_INVALID_ARG, "NULL output array");
+  return PMA_OK;
+}
+
+static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
+                   const void *const *mom, const void *weights, double tol_x, double tol_p,
+                   const pma_output *out, cudaStream_t st) {
+  const int64_t C = h->cfg.n_cells;
+  PMA_CUDA(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), st));
+  if (n == 0) {
+    if (out->count_dev) PMA_CUDA(h, cudaMemsetAsync(out->count_dev, 0, sizeof(int64_t), st));
+    return PMA_OK;
+  }
+  PMA_CUDA(h, cudaMemsetAsync(h->counts, 0, C * sizeof(int32_t), st));
+  PMA_CUDA(h, cudaMemsetAsync(h->fill, 0, C * sizeof(int32_t), st));
+  PMA_CUDA(h, cudaMemsetAsync(h->bin_status, 0, h->bin_tiles * sizeof(unsigned long long), st));
+  const int tiles = emit_tiles_for(n);
+  PMA_CUDA(h, cudaMemsetAsync(h->emit_status, 0, tiles * sizeof(unsigned long long), st));
+
+  BinArgs b{};
+  b.n = n;
+  b.cells = cells;
+  b.n_cells = (int32_t)C;
+  b.cap = h->cap;
+  b.n_min = h->cfg.n_min;
+  b.counts = h->counts;
+  b.cell_begin = h->cell_begin;
+  b.fill = h->fill;
+  b.perm = h->perm;
+  b.unsorted = &h->ctl->unsorted;
+  b.big_list = h->big_list;
+  b.big_count = &h->ctl->big_count;
+  b.err = &h->ctl->err;
+  b.scan_status = h->bin_status;
+  b.scan_ticket = &h->ctl->bin_ticket;
+  b.scan_tiles = h->bin_tiles;
+  h->cur_ev = h->timing ? h->ev[h->timed % kRing] : nullptr;
+  mark(h, 0, st);
+  cudaError_t e = launch_binning(b, h->sms, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "binning launch");
+  mark(h, 1, st);
+
+  Problem P{};
+  P.n_cells = (int32_t)C;
+  P.dx = h->cfg.dx;
+  P.D = h->D;
+  P.n_min = h->cfg.n_min;
+  P.cap = h->cap;
+  P.unsorted = &h->ctl->unsorted;
+  P.tol2_x = tol_x * tol_x;
+  P.tol2_p = tol_p * tol_p;
+  P.tol2_xf = (float)P.tol2_x;
+  P.tol2_pf = (float)P.tol2_p;
+  for (int a = 0; a < 3; ++a) {
+    double L = a < h->cfg.dx ? h->cfg.cell_size[a] : 1.0;
+    P.L2[a] = L * L;
+    P.L2f[a] = (float)P.L2[a];
+  }
+  for (int a = 0; a < h->cfg.dx; ++a) P.q[a] = pos[a];
+  for (int a = 0; a < h->cfg.dp; ++a) P.q[h->cfg.dx + a] = mom[a];
+  P.w = weights;
+  P.cells = cells;
+  P.cell_begin = h->cell_begin;
+  P.perm = h->perm;
+  P.head = h->head;
+  P.perm_final = h->perm_final;
+  P.rec_w = h->rec_w;
+  P.rec_c = h->rec_c;
+  P.stride = h->capacity;
+  P.err = &h->ctl->err;
+  P.stats = h->ctl->stats;
+  P.big_list = h->big_list;
+  P.big_count = &h->ctl->big_count;
+  P.big_next = &h->ctl->big_next;
+  P.pieces = h->pieces;
+  P.piece_count = &h->ctl->piece_count;
+  P.perm_tmp = h->perm_tmp;
+  P.max_pieces = h->max_pieces;
+  P.unit_next = h->ctl->unit_next;
+
+  e = launch_big(P, h->mixed, h->sms, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
+  mark(h, 2, st);
+  e = launch_units(P, h->mixed, 0, h->unit_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (cells)");
+  mark(h, 3, st);
+  e = launch_units(P, h->mixed, 1, h->unit_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (pieces)");
+  mark(h, 4, st);
+
+  EmitArgs m{};
+  m.n = n;
+  m.dx = h->cfg.dx;
+  m.dp = h->cfg.dp;
+  m.mixed = h->mixed;
+  m.head = h->head;
+  m.perm_final = h->perm_final;
+  m.rec_w = h->rec_w;
+  m.rec_c = h->rec_c;
+  m.stride = h->capacity;
+  m.cells = cells;
+  for (int l = 0; l < h->D; ++l) m.q[l] = P.q[l];
+  m.w = weights;
+  m.out_cell = out->cell;
+  for (int a = 0; a < 3; ++a) {
+    m.out_pos[a] = out->pos[a];
+    m.out_mom[a] = out->mom[a];
+  }
+  m.out_w = out->w;
+  m.out_index = (h->cfg.flags & PMA_FLAG_NO_INDEX) ? nullptr : out->index;
+  m.out_count = out->count_dev;
+  m.out_count2 = &h->ctl->count;
+  m.err = &h->ctl->err;
+  m.scan_status = h->emit_status;
+  m.scan_ticket = &h->ctl->emit_ticket;
+  m.tiles = tiles;
+  e = launch_emit(m, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "emit launch");
+  mark(h, 5, st);
+  if (h->timing) ++h->timed;
+  return PMA_OK;
+}
+
+int pma_merge(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
+              const void *const *mom, const void *weights, double tol_x, double tol_p,
+              const pma_output *out, int64_t *count_host, void *stream) {
+  int rc = check_common(h, n, cells, pos, mom, weights, tol_x, tol_p, out);
+  if (rc != PMA_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = -1;
+  PMA_CUDA(h, cudaGetDevice(&dev));
+  if (dev != h->device) return fail(h, PMA_ERR_INVALID_ARG, "handle belongs to another device");
+  rc = enqueue(h, n, cells, pos, mom, weights, tol_x, tol_p, out, st);
+  if (rc != PMA_OK) return rc;
+  h->stats = pma_stats{};
+  h->stats.n_in = n;
+  PMA_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  h->last_stream = st;
+  h->pending = true;
+  if (!count_host) return PMA_OK;
+  rc = pma_sync(h);
+  *count_host = h->stats.n_out;
+  return rc;
+}
+
+int pma_sync(pma_handle *h) {
+  if (!h) return PMA_ERR_INVALID_ARG;
+  if (!h->pending) return PMA_OK;
+  cudaError_t e = cudaStreamSynchronize(h->last_stream);
+  h->pending = false;
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+  int64_t n_in = h->stats.n_in;
+  int rc = status_from_ctl(h);
+  h->stats.n_in = n_in;
+  return rc;
+}
+
+int pma_set_timing(pma_handle *h, int enable) {
+  if (!h) return PMA_ERR_INVALID_ARG;
+  if (enable && !h->ev[0][0]) {
+    for (auto &row : h->ev)
+      for (auto &e : row)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(h, PMA_ERR_CUDA, "cudaEventCreate");
+  }
+  h->timing = enable != 0;
+  h->timed = 0;
+  return PMA_OK;
+}
+
+int pma_get_timing(const pma_handle *h, float *ms, int n) {
+  if (!h || !ms || h->timed == 0) return PMA_ERR_INVALID_ARG;
+  static const int from[PMA_N_STAGES] = {0, 1, 2, 3, 4, 0};
+  static const int to[PMA_N_STAGES] = {1, 2, 3, 4, 5, 5};
+  const int calls = h->timed < kRing ? h->timed : kRing;
+  for (int i = 0; i < n && i < PMA_N_STAGES; ++i) {
+    double sum = 0.0;
+    for (int c = 0; c < calls; ++c) {
+      float t = 0.f;
+      if (cudaEventSynchronize(h->ev[c][to[i]]) != cudaSuccess ||
+          cudaEventElapsedTime(&t, h->ev[c][from[i]], h->ev[c][to[i]]) != cudaSuccess)
+        return PMA_ERR_CUDA;
+      sum += t;
+    }
+    ms[i] = (float)(sum / calls);
+  }
+  return PMA_OK;
+}
+
+int pma_get_stats(const pma_handle *h, pma_stats *out) {
+  if (!h || !out) return PMA_ERR_INVALID_ARG;
+  *out = h->stats;
+  return PMA_OK;
+}
+
+int pma_merge_host(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
+                   const void *const *mom, const void *weights, double tol_x, double tol_p,
+                   const pma_output *out_host, int64_t *count_host, void *stream) {
+  int rc = check_common(h, n, cells, pos, mom, weights, tol_x, tol_p, out_host);
+  if (rc != PMA_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Staging &S = h->stage;
+  const size_t N = (size_t)std::max<int64_t>(h->capacity, 1);
+  const size_t ts = h->mixed ? sizeof(float) : sizeof(double);
+  if (!S.ready) {
+    bool ok = dalloc(&S.cells, N) == cudaSuccess && dalloc(&S.out_cell, N) == cudaSuccess &&
+              dalloc(&S.out_w, N) == cudaSuccess && dalloc(&S.out_index, N) == cudaSuccess &&
+              cudaMalloc(&S.w, N * ts) == cudaSuccess;
+    for (int l = 0; ok && l < h->D; ++l) ok = cudaMalloc(&S.q[l], N * ts) == cudaSuccess;
+    for (int a = 0; ok && a < h->cfg.dx; ++a) ok = cudaMalloc(&S.out_pos[a], N * ts) == cudaSuccess;
+    for (int a = 0; ok && a < h->cfg.dp; ++a) ok = dalloc(&S.out_mom[a], N) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return fail(h, PMA_ERR_NOMEM, "staging buffers");
+    }
+    S.ready = true;
+  }
+  if (n > 0) {
+    PMA_CUDA(h, cudaMemcpyAsync(S.cells, cells, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    for (int a = 0; a < h->cfg.dx; ++a)
+      PMA_CUDA(h, cudaMemcpyAsync(S.q[a], pos[a], n * ts, cudaMemcpyHostToDevice, st));
+    for (int a = 0; a < h->cfg.dp; ++a)
+      PMA_CUDA(h, cudaMemcpyAsync(S.q[h->cfg.dx + a], mom[a], n * ts, cudaMemcpyHostToDevice, st));
+    PMA_CUDA(h, cudaMemcpyAsync(S.w, weights, n * ts, cudaMemcpyHostToDevice, st));
+  }
+  pma_output dout{};
+  dout.cell = S.out_cell;
+  for (int a = 0; a < 3; ++a) {
+    dout.pos[a] = S.out_pos[a];
+    dout.mom[a] = S.out_mom[a];
+  }
+  dout.w = S.out_w;
+  dout.index = out_host->index ? S.out_index : nullptr;
+  const void *dq[3], *dm[3];
+  for (int a = 0; a < h->cfg.dx; ++a) dq[a] = S.q[a];
+  for (int a = 0; a < h->cfg.dp; ++a) dm[a] = S.q[h->cfg.dx + a];
+  int64_t M = 0;
+  rc = pma_merge(h, n, S.cells, dq, dm, S.w, tol_x, tol_p, &dout, &M, stream);
+  if (rc != PMA_OK) return rc;
+  if (M > 0) {
+    PMA_CUDA(h, cudaMemcpyAsync(out_host->cell, S.out_cell, M * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < h->cfg.dx; ++a)
+      PMA_CUDA(h, cudaMemcpyAsync(out_host->pos[a], S.out_pos[a], M * ts, cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < h->cfg.dp; ++a)
+      PMA_CUDA(h, cudaMemcpyAsync(out_host->mom[a], S.out_mom[a], M * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st));
+    PMA_CUDA(h, cudaMemcpyAsync(out_host->w, S.out_w, M * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  if (out_host->index && n > 0)
+    PMA_CUDA(h, cudaMemcpyAsync(out_host->index, S.out_index, n * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, st));
+  PMA_CUDA(h, cudaStreamSynchronize(st));
+  if (count_host) *count_host = M;
+  return PMA_OK;
+}
+
+}  // extern "C"

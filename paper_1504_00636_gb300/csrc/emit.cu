@@ -1,0 +1,123 @@
+// Step 7: replace every final set by its centroid, compacted in canonical
+// order.  The final sets of all cells are contiguous position ranges marked by
+// a head byte at their first position; cells are laid out in ascending order
+// and the sets of a cell in V1-first depth-first order, so the output slot of
+// a set is the number of heads before it.  One pass: each tile counts its
+// heads, gets its exclusive prefix by decoupled look-back, and writes the
+// merged particles and the input->output index.
+#include "lookback.cuh"
+#include "pma_launch.h"
+
+namespace pma {
+
+constexpr int kEmitThreads = 256;
+constexpr int kEmitChunk = 16;  // consecutive positions per chunk
+constexpr int kEmitTile = kEmitThreads * kEmitChunk;
+
+int emit_tiles_for(int64_t n) { return (int)((n + kEmitTile - 1) / kEmitTile); }
+
+template <typename T>
+__device__ __forceinline__ double to_f64(T x);
+template <>
+__device__ __forceinline__ double to_f64<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ double to_f64<float>(float x) {
+  return f2d_exact(x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
+  __shared__ int s_tile;
+  __shared__ int s_warp[32];
+  __shared__ long long s_prefix;
+  __shared__ unsigned short s_mask[kEmitThreads];
+  __shared__ int s_chunk[kEmitThreads];
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(a.scan_ticket, 1);
+  __syncthreads();
+  const int tile = s_tile;
+  const int64_t t0 = (int64_t)tile * kEmitTile;
+  // heads of my chunk of 16 consecutive positions
+  const int64_t c0 = t0 + (int64_t)tid * kEmitChunk;
+  unsigned mask = 0;
+  if (c0 + kEmitChunk <= a.n) {
+    uint4 hv = *reinterpret_cast<const uint4 *>(a.head + c0);
+    unsigned wv[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if ((wv[j >> 2] >> (8 * (j & 3))) & 0xffu) mask |= 1u << j;
+  } else {
+    for (int j = 0; j < kEmitChunk; ++j)
+      if (c0 + j < a.n && a.head[c0 + j]) mask |= 1u << j;
+  }
+  int total;
+  int ex = block_exclusive_scan(__popc(mask), s_warp, &total);
+  s_mask[tid] = (unsigned short)mask;
+  s_chunk[tid] = ex;
+  if (tid == 0) {
+    long long pre = tile_exclusive_prefix(a.scan_status, tile, total, a.err);
+    s_prefix = pre;
+    if (tile == a.tiles - 1) {
+      if (a.out_count) *a.out_count = pre + total;
+      if (a.out_count2) *a.out_count2 = pre + total;
+    }
+  }
+  __syncthreads();
+  const long long prefix = s_prefix;
+  // positions in strided order: consecutive threads, consecutive positions
+  bool bad = false, internal = false;
+  for (int j = 0; j < kEmitChunk; ++j) {
+    const int off = j * kEmitThreads + tid;
+    const int64_t p = t0 + off;
+    if (p >= a.n) break;
+    const int ch = off / kEmitChunk, in = off % kEmitChunk;
+    const unsigned m = s_mask[ch];
+    const long long slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
+    const int orig = a.perm_final[p];
+    if ((unsigned)orig >= (unsigned)a.n) {
+      // a position left unwritten by an earlier failure: never follow it
+      internal = true;
+      continue;
+    }
+    if (a.out_index) a.out_index[orig] = (int32_t)slot;
+    if (!((m >> in) & 1u)) continue;
+    const uint8_t h = a.head[p];
+    a.out_cell[slot] = a.cells[orig];
+    if (h == kHeadSingle) {
+      // one-particle set: the particle itself (Step 7)
+      for (int l = 0; l < a.dx; ++l) {
+        T x = static_cast<const T *>(a.q[l])[orig];
+        bad |= !isfinite(x);
+        static_cast<T *>(a.out_pos[l])[slot] = x;
+      }
+      for (int l = 0; l < a.dp; ++l) {
+        T x = static_cast<const T *>(a.q[a.dx + l])[orig];
+        bad |= !isfinite(x);
+        a.out_mom[l][slot] = to_f64<T>(x);
+      }
+      T w = static_cast<const T *>(a.w)[orig];
+      bad |= !(w > T(0)) || !isfinite(w);
+      a.out_w[slot] = to_f64<T>(w);
+    } else {
+      a.out_w[slot] = a.rec_w[p];
+      for (int l = 0; l < a.dx; ++l)
+        static_cast<T *>(a.out_pos[l])[slot] = (T)a.rec_c[l * a.stride + p];
+      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot] = a.rec_c[(a.dx + l) * a.stride + p];
+    }
+  }
+  if (bad) atomicOr(a.err, kErrInput);
+  if (internal) atomicOr(a.err, kErrInternal);
+}
+
+cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
+  if (a.tiles <= 0) return cudaSuccess;
+  if (a.mixed)
+    emit_kernel<float><<<a.tiles, kEmitThreads, 0, st>>>(a);
+  else
+    emit_kernel<double><<<a.tiles, kEmitThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace pma

@@ -1,0 +1,96 @@
+// Single-pass exclusive prefix over tiles with decoupled look-back: a tile
+// publishes its own count, then walks back over its predecessors until it
+// meets one whose inclusive prefix is known.  Tiles are numbered by an atomic
+// ticket, so every predecessor belongs to a CTA that is already running.
+// The walk gives up after a bounded time, sets kErrTimeout and returns.
+#pragma once
+
+#include <cstdint>
+
+#include "pma_device.cuh"
+
+namespace pma {
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Called by one thread of the tile; returns the exclusive prefix of `tile`.
+__device__ inline long long tile_exclusive_prefix(unsigned long long *status, int tile,
+                                                  long long aggregate, unsigned *err) {
+  if (tile == 0) {
+    st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
+    return 0;
+  }
+  st_release_u64(&status[tile], kFlagAgg | (unsigned long long)aggregate);
+  long long prefix = 0;
+  int t = tile - 1;
+  unsigned long long t0 = 0;
+  while (t >= 0) {
+    unsigned long long s = ld_acquire_u64(&status[t]);
+    unsigned long long f = s >> 62;
+    if (f == 0) {
+      unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(64);
+      continue;
+    }
+    prefix += (long long)(s & kValMask);
+    if (f == 2) break;
+    --t;
+  }
+  st_release_u64(&status[tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+  return prefix;
+}
+
+// exclusive scan of one int per thread across the CTA (blockDim <= 1024);
+// `warp_sums` holds 32 ints of shared memory; returns the block total in *total
+__device__ inline int block_exclusive_scan(int v, int *warp_sums, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, d);
+      if (lane >= d) s += y;
+    }
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int before = warp > 0 ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+}  // namespace pma

@@ -1,0 +1,335 @@
+// Device-side building blocks of the Voronoi merge (Sec. 3, Steps 1-7 of
+// Luu, Tueckmantel & Pukhov, arXiv:1504.00636).
+//
+// Notation follows the paper: a subset V has weight W = sum w, centroid
+// (X, P) = sum w q / W, per-axis standard deviation sigma and coefficient of
+// variation Delta (Eqs. cv_x, cv_p).  Moments are accumulated about a shift
+// s (the subset's first particle): W, m1_l = sum w (q_l - s_l) and
+// m2_l = sum w (q_l - s_l)^2, so that
+//     W^2 var_l = m2_l W - m1_l^2,     W Q_l = s_l W + m1_l.
+// Step 3 and Step 4 then need no square root or division:
+//     Delta_l <= T    <=>  W^2 var_l <= T^2 den_l,
+//     Delta_a > Delta_b  <=>  (W^2 var_a) den_b > (W^2 var_b) den_a,
+// with den_l = (L_l W)^2 on a position axis and (W Q_l)^2 on a momentum axis
+// (den = 0 and var > 0 is Delta = +infinity; var = 0 is Delta = 0).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pma {
+
+constexpr int kMaxD = 6;
+
+// error bits of the device status word
+constexpr unsigned kErrInput = 1u;
+constexpr unsigned kErrInternal = 2u;
+constexpr unsigned kErrTimeout = 4u;
+
+// counters kept on the device (indices into Problem::stats)
+enum Stat {
+  kStCellsMerged = 0,
+  kStCellsPass,
+  kStSplits,
+  kStLeaves,
+  kStDepth,
+  kStDegenerate,
+  kStBig,
+  kStSorted,
+  kStCount
+};
+
+// head byte of a final position: 0 inside a final set, 1 first (only)
+// particle of a one-particle set, 2 first particle of a merged set whose
+// centroid record sits at that position
+constexpr uint8_t kHeadSingle = 1;
+constexpr uint8_t kHeadMerged = 2;
+
+struct Problem {
+  int32_t n_cells;
+  int32_t dx;
+  int32_t D;
+  int32_t n_min;
+  int32_t cap;          // particles per unit held in shared memory
+  const int32_t *unsorted;  // device flag: 0 when cell ids are non-decreasing
+  double tol2_x, tol2_p;  // T^2
+  double L2[3];           // L^2 per position axis
+  float tol2_xf, tol2_pf;
+  float L2f[3];
+  const void *q[kMaxD];   // input coordinates by axis: positions, then momenta
+  const void *w;          // input weights
+  const int32_t *cells;   // input cell ids
+  const int32_t *cell_begin;  // [n_cells + 1] first sorted position of each cell
+  int32_t *perm;          // sorted position -> input index (workspace)
+  uint8_t *head;          // [N] head byte per final position
+  int32_t *perm_final;    // [N] input index at each final position
+  double *rec_w;          // [N] centroid weight at merged-set heads
+  double *rec_c;          // [D][stride] centroid coordinates
+  int64_t stride;
+  unsigned *err;          // device status word
+  unsigned long long *stats;
+  // big cells: cells above `cap` are cut in global memory first
+  int32_t *big_list;
+  int32_t *big_count;
+  int32_t *big_next;
+  int4 *pieces;           // {begin, end, depth, 0}
+  int32_t *piece_count;
+  int32_t *perm_tmp;
+  int32_t max_pieces;
+  int32_t *unit_next;     // ticket counters of the unit kernel, one per mode
+};
+
+// ------------------------------------------------------------ accumulators
+
+template <typename T>
+struct Acc;
+
+// plain FP64 sum
+template <>
+struct Acc<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void merge(const Acc &o) { v += o.v; }
+  __device__ __forceinline__ void shfl_xor(int m) { v += __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ __forceinline__ double hi() const { return v; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+// compensated (Kahan) FP32 sum: value = s - c
+template <>
+struct Acc<float> {
+  float s, c;
+  __device__ __forceinline__ void zero() {
+    s = 0.f;
+    c = 0.f;
+  }
+  __device__ __forceinline__ void add(float x) {
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  // exact two-sum of the leading parts, errors folded into c
+  __device__ __forceinline__ void merge2(float s2, float c2) {
+    float t = __fadd_rn(s, s2);
+    float bp = __fsub_rn(t, s);
+    float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    c = __fsub_rn(__fadd_rn(c, c2), e);
+    s = t;
+  }
+  __device__ __forceinline__ void merge(const Acc &o) { merge2(o.s, o.c); }
+  __device__ __forceinline__ void shfl_xor(int m) {
+    float s2 = __shfl_xor_sync(0xffffffffu, s, m);
+    float c2 = __shfl_xor_sync(0xffffffffu, c, m);
+    merge2(s2, c2);
+  }
+  __device__ __forceinline__ float hi() const { return s; }
+  __device__ __forceinline__ float lo() const { return -c; }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename T, int D>
+struct Moments {
+  Acc<T> W;
+  Acc<T> m1[D];
+  Acc<T> m2[D];
+  __device__ __forceinline__ void zero() {
+    W.zero();
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      m1[l].zero();
+      m2[l].zero();
+    }
+  }
+  __device__ __forceinline__ void add(T w, const T *q, const T *s) {
+    W.add(w);
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      T d = q[l] - s[l];
+      T t = w * d;
+      m1[l].add(t);
+      m2[l].add(t * d);
+    }
+  }
+  __device__ __forceinline__ void merge(const Moments &o) {
+    W.merge(o.W);
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      m1[l].merge(o.m1[l]);
+      m2[l].merge(o.m2[l]);
+    }
+  }
+  __device__ __forceinline__ void warp_allreduce() {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      W.shfl_xor(m);
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        m1[l].shfl_xor(m);
+        m2[l].shfl_xor(m);
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------- decisions
+
+struct Cut {
+  int leaf;   // Step 3 stop test passed
+  int k;      // Step 4 axis
+  double Q;   // Step 5 centroid coordinate on axis k (FP64)
+  float Qt;   // largest float <= Q (FP32 storage: q <= Q  <=>  q <= Qt)
+};
+
+// Steps 3-5 in FP64 from moment values (W, m1, m2 about the shift s).
+template <int D>
+__device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const double *m1,
+                                           const double *m2, const double *s) {
+  Cut c;
+  c.leaf = 1;
+  c.k = 0;
+  double bestV = -1.0, bestDen = 1.0;
+  double W2 = W * W;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    double V = fmax(fma(m2[l], W, -m1[l] * m1[l]), 0.0);
+    double den, tol2;
+    if (l < P.dx) {
+      den = P.L2[l] * W2;
+      tol2 = P.tol2_x;
+    } else {
+      double Pw = fma(s[l], W, m1[l]);
+      den = Pw * Pw;
+      tol2 = P.tol2_p;
+    }
+    // Delta_l <= T  <=>  V <= T^2 den  (den = 0: only V = 0 passes)
+    if (!(V <= tol2 * den)) c.leaf = 0;
+    // first maximum of Delta_l = sqrt(V / den)
+    if (bestV < 0.0 || V * bestDen > bestV * den) {
+      bestV = V;
+      bestDen = den;
+      c.k = l;
+    }
+  }
+  double Q = s[0];
+#pragma unroll
+  for (int l = 0; l < D; ++l)
+    if (l == c.k) Q = s[l] + m1[l] / W;
+  c.Q = Q;
+  c.Qt = __double2float_rd(Q);
+  return c;
+}
+
+// Step 3-5 for compensated FP32 moments.  The stop test and the axis choice
+// are evaluated in FP32 with an error bound; when a comparison is closer
+// than the bound the FP64 evaluation of the same sums decides.  The cut value
+// is computed as a double-float (hi + lo) and rounded down to float.
+template <int D>
+__device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<float, D> &M,
+                                            const float *s) {
+  const float g = 1.0f / (1 << 19);  // error budget relative to the terms
+  float W = M.W.hi();
+  float W2 = W * W;
+  Cut c;
+  c.leaf = 1;
+  c.k = 0;
+  bool sure = true;
+  float r[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    float m1 = M.m1[l].hi(), m2 = M.m2[l].hi();
+    float a = m2 * W, b = m1 * m1;
+    float V = fmaxf(a - b, 0.f);
+    float eV = g * (fabsf(a) + b);
+    float den, eD, tol2;
+    if (l < P.dx) {
+      den = P.L2f[l] * W2;
+      eD = g * den;
+      tol2 = P.tol2_xf;
+    } else {
+      float Pw = fmaf(s[l], W, m1);
+      float eP = g * (fabsf(s[l] * W) + fabsf(m1));
+      den = Pw * Pw;
+      eD = 2.f * fabsf(Pw) * eP + eP * eP + g * den;
+      tol2 = P.tol2_pf;
+    }
+    float f = V - tol2 * den;
+    if (fabsf(f) <= eV + tol2 * eD) sure = false;
+    if (f > 0.f) c.leaf = 0;
+    // Delta^2 with relative uncertainty; den = 0 means infinity unless V = 0
+    if (V == 0.f)
+      r[l] = 0.f;
+    else if (den <= eD)
+      r[l] = __int_as_float(0x7f800000);
+    else
+      r[l] = V / den;
+    if (V != 0.f && (V <= eV || den <= eD)) sure = false;
+  }
+  if (!c.leaf) {
+    int k = 0;
+#pragma unroll
+    for (int l = 1; l < D; ++l)
+      if (r[l] > r[k]) k = l;
+    c.k = k;
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l != k && r[l] >= r[k] * (1.f - 64.f * g)) sure = false;
+  }
+  if (!sure) {
+    double W64 = M.W.value(), m1d[D], m2d[D], sd[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      m1d[l] = M.m1[l].value();
+      m2d[l] = M.m2[l].value();
+      sd[l] = (double)s[l];
+    }
+    Cut d = decide_fp64<D>(P, W64, m1d, m2d, sd);
+    d.Q = 0.0;
+    c.leaf = d.leaf;
+    c.k = d.k;
+  }
+  if (c.leaf) return c;
+  // cut value Q = s_k + m1_k / W as a double-float, then rounded down
+  float sk = s[0], m1h = M.m1[0].hi(), m1l = M.m1[0].lo();
+#pragma unroll
+  for (int l = 0; l < D; ++l)
+    if (l == c.k) {
+      sk = s[l];
+      m1h = M.m1[l].hi();
+      m1l = M.m1[l].lo();
+    }
+  float Wh = M.W.hi(), Wl = M.W.lo();
+  float q0 = __fdiv_rn(m1h, Wh);
+  float p = q0 * Wh;
+  float pe = fmaf(q0, Wh, -p);
+  float rr = ((m1h - p) - pe) + m1l - q0 * Wl;
+  float q1 = rr / Wh;
+  // (h, e) = TwoSum(sk, q0)
+  float h = __fadd_rn(sk, q0);
+  float bp = __fsub_rn(h, sk);
+  float e = __fadd_rn(__fsub_rn(sk, __fsub_rn(h, bp)), __fsub_rn(q0, bp));
+  float lo = __fadd_rn(e, q1);
+  float Qh = __fadd_rn(h, lo);
+  float Ql = __fsub_rn(lo, __fsub_rn(Qh, h));
+  c.Qt = (Ql < 0.f) ? __int_as_float(__float_as_int(Qh) - (Qh > 0.f ? 1 : (Qh < 0.f ? -1 : 0)))
+                    : Qh;
+  if (Qh == 0.f && Ql < 0.f) c.Qt = -__int_as_float(1);  // largest float below zero
+  c.Q = (double)Qh + (double)Ql;
+  return c;
+}
+
+// FP32 -> FP64 without the FP64 pipe (exact for every finite float).
+__device__ __forceinline__ double f2d_exact(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;  // zero, subnormal, inf, nan
+  unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  unsigned long long ee = (unsigned long long)(e + 896u) << 52;
+  unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(s | ee | m));
+}
+
+__device__ __forceinline__ void set_error(unsigned *err, unsigned bit) { atomicOr(err, bit); }
+
+}  // namespace pma

@@ -1,0 +1,65 @@
+// Host-side launchers shared by the translation units of the library.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "pma_device.cuh"
+
+namespace pma {
+
+// split.cu
+size_t unit_smem(int mixed, int D, int cap);
+cudaError_t launch_units(const Problem &P, int mixed, int mode, int grid, cudaStream_t st);
+cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st);
+
+// bin.cu
+struct BinArgs {
+  int64_t n;
+  const int32_t *cells;
+  int32_t n_cells;
+  int32_t cap;
+  int32_t n_min;
+  int32_t *counts;      // [n_cells]
+  int32_t *cell_begin;  // [n_cells + 1]
+  int32_t *fill;        // [n_cells]
+  int32_t *perm;        // [n]
+  int32_t *unsorted;    // device flag
+  int32_t *big_list;
+  int32_t *big_count;
+  unsigned *err;
+  unsigned long long *scan_status;  // [scan tiles]
+  int32_t *scan_ticket;
+  int32_t scan_tiles;
+};
+cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st);
+int scan_tiles_for(int64_t n);
+
+// emit.cu
+struct EmitArgs {
+  int64_t n;
+  int32_t dx, dp, mixed;
+  const uint8_t *head;
+  const int32_t *perm_final;
+  const double *rec_w;
+  const double *rec_c;
+  int64_t stride;
+  const int32_t *cells;
+  const void *q[kMaxD];
+  const void *w;
+  int32_t *out_cell;
+  void *out_pos[3];
+  double *out_mom[3];
+  double *out_w;
+  int32_t *out_index;
+  int64_t *out_count;   // device word(s) receiving M
+  int64_t *out_count2;
+  unsigned *err;
+  unsigned long long *scan_status;
+  int32_t *scan_ticket;
+  int32_t tiles;
+};
+int emit_tiles_for(int64_t n);
+cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st);
+
+}  // namespace pma

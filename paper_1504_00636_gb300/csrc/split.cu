@@ -1,0 +1,706 @@
+// Recursive Voronoi partition of every cell (Sec. 3, Steps 2-6) and the
+// centroid records of its final sets (Step 7).
+//
+// unit_kernel: one CTA per unit (a whole cell, or a piece of a big cell),
+// particles staged in shared memory as SoA columns, double-buffered by tree
+// depth parity.  A subset is always a contiguous range [b, e) of one buffer;
+// a cut writes V1 = {q_k <= Q_k} to the front and V2 to the back of the same
+// range in the other buffer, so the final sets of a cell end up in V1-first
+// depth-first order when listed by position.
+//   phase A: subsets larger than kSmall are handled one per warp, level by
+//            level (moments by warp reduction, cut by ballot scan);
+//   phase B: subsets of at most kSmall particles are finished by one thread
+//            each, depth-first.
+// big_kernel: cells larger than the shared-memory capacity are cut by a whole
+// CTA in global memory (on the permutation array only) until every piece
+// fits; the pieces then go through unit_kernel.
+#include "pma_device.cuh"
+#include "pma_launch.h"
+
+namespace pma {
+
+constexpr int kSmall = 32;
+
+struct Item {
+  uint16_t b, e;
+  uint8_t par, depth;
+  uint16_t pad;
+};
+
+template <typename T>
+struct StoreOf {
+  __device__ static __forceinline__ T load(const void *p, int64_t i) {
+    return static_cast<const T *>(p)[i];
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T x) {
+  return isfinite(x);
+}
+
+// ------------------------------------------------------------ cut helpers
+
+template <typename T, int D>
+struct Decider;
+
+template <int D>
+struct Decider<double, D> {
+  __device__ static __forceinline__ Cut run(const Problem &P, const Moments<double, D> &M,
+                                            const double *s) {
+    double m1[D], m2[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      m1[l] = M.m1[l].v;
+      m2[l] = M.m2[l].v;
+    }
+    return decide_fp64<D>(P, M.W.v, m1, m2, s);
+  }
+  __device__ static __forceinline__ bool left(double q, const Cut &c) { return q <= c.Q; }
+};
+
+template <int D>
+struct Decider<float, D> {
+  __device__ static __forceinline__ Cut run(const Problem &P, const Moments<float, D> &M,
+                                            const float *s) {
+    return decide_mixed<D>(P, M, s);
+  }
+  __device__ static __forceinline__ bool left(float q, const Cut &c) { return q <= c.Qt; }
+};
+
+// centroid record of a merged set, from its moments (FP64 storage)
+template <int D>
+__device__ __forceinline__ void record_from_moments(const Problem &P, int64_t pos,
+                                                    const Moments<double, D> &M,
+                                                    const double *s) {
+  double W = M.W.v;
+  P.rec_w[pos] = W;
+#pragma unroll
+  for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + pos] = s[l] + M.m1[l].v / W;
+}
+
+// ---------------------------------------------------------- shared layout
+
+template <typename T, int D>
+struct Tile {
+  T *base;
+  uint16_t *id[2];
+  int cap;
+  __device__ __forceinline__ T *col(int par, int l) const {
+    return base + (size_t)(par * (D + 1) + l) * cap;
+  }
+};
+
+template <typename T, int D>
+__host__ __device__ inline size_t unit_smem_bytes(int cap) {
+  size_t v = (size_t)2 * (D + 1) * cap * sizeof(T);
+  size_t ids = (size_t)2 * cap * sizeof(uint16_t);
+  size_t lists = (size_t)(2 * (cap / kSmall + 2) + (cap / 2 + 2)) * sizeof(Item);
+  return v + ids + lists;
+}
+
+__device__ __forceinline__ int orig_index(const int32_t *perm, int64_t gb, int j) {
+  return perm ? perm[gb + j] : (int)(gb + j);
+}
+
+// ------------------------------------------------------- leaf emission
+
+// merged set [b, e) of buffer `par`, by one warp
+template <typename T, int D>
+__device__ void emit_leaf_warp(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
+                               int64_t gb, int b, int e, int par, const Moments<T, D> &M,
+                               const T *s, int lane) {
+  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
+  for (int j = b + lane; j < e; j += 32) {
+    P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
+    P.head[gb + j] = (j == b) ? h : (uint8_t)0;
+  }
+  int64_t hp = gb + b;
+  if (e - b == 1) return;
+  if constexpr (sizeof(T) == 8) {
+    if (lane == 0) record_from_moments<D>(P, hp, M, s);
+  } else {
+    // merged W and P in FP64: products of two floats are exact in FP64
+    double W = 0.0, S1[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) S1[l] = 0.0;
+    for (int j = b + lane; j < e; j += 32) {
+      double w = f2d_exact(S.col(par, D)[j]);
+      W += w;
+#pragma unroll
+      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(par, l)[j]), S1[l]);
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      W += __shfl_xor_sync(0xffffffffu, W, m);
+#pragma unroll
+      for (int l = 0; l < D; ++l) S1[l] += __shfl_xor_sync(0xffffffffu, S1[l], m);
+    }
+    if (lane == 0) {
+      P.rec_w[hp] = W;
+#pragma unroll
+      for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
+    }
+  }
+}
+
+// merged set [b, e) of buffer `par`, by one thread
+template <typename T, int D>
+__device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
+                                 int64_t gb, int b, int e, int par, const Moments<T, D> &M,
+                                 const T *s) {
+  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
+  for (int j = b; j < e; ++j) {
+    P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
+    P.head[gb + j] = (j == b) ? h : (uint8_t)0;
+  }
+  int64_t hp = gb + b;
+  if (e - b == 1) return;
+  if constexpr (sizeof(T) == 8) {
+    record_from_moments<D>(P, hp, M, s);
+  } else {
+    double W = 0.0, S1[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) S1[l] = 0.0;
+    for (int j = b; j < e; ++j) {
+      double w = f2d_exact(S.col(par, D)[j]);
+      W += w;
+#pragma unroll
+      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(par, l)[j]), S1[l]);
+    }
+    P.rec_w[hp] = W;
+#pragma unroll
+    for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
+  }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// --------------------------------------------------------------- phase A
+
+template <typename T, int D>
+__device__ void warp_split(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
+                           int64_t gb, Item it, Item *nxt, int *n_nxt, int max_nxt,
+                           Item *small, int *n_small, unsigned long long *st, int lane) {
+  const int b = it.b, e = it.e, par = it.par;
+  T s[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) s[l] = S.col(par, l)[b];
+  Moments<T, D> M;
+  M.zero();
+  for (int i = b + lane; i < e; i += 32) {
+    T q[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) q[l] = S.col(par, l)[i];
+    M.add(S.col(par, D)[i], q, s);
+  }
+  M.warp_allreduce();
+  Cut c = Decider<T, D>::run(P, M, s);
+  if (c.leaf) {
+    emit_leaf_warp<T, D>(P, S, perm, gb, b, e, par, M, s, lane);
+    if (lane == 0) {
+      atomicAdd(&st[kStLeaves], 1ull);
+      atomicAdd(&st[kStDepth], (unsigned long long)it.depth * (e - b));
+    }
+    return;
+  }
+  const int np = par ^ 1;
+  const T *qk = S.col(par, c.k);
+  int cntL = 0, cntR = 0;
+  const unsigned lt = lanemask_lt();
+  for (int base = b; base < e; base += 32) {
+    int i = base + lane;
+    bool valid = i < e;
+    bool lft = valid && Decider<T, D>::left(qk[valid ? i : b], c);
+    unsigned bl = __ballot_sync(0xffffffffu, lft);
+    unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+    if (valid) {
+      int dst = lft ? (b + cntL + __popc(bl & lt)) : (e - 1 - cntR - __popc(br & lt));
+#pragma unroll
+      for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
+      S.id[np][dst] = S.id[par][i];
+    }
+    cntL += __popc(bl);
+    cntR += __popc(br);
+  }
+  __syncwarp();
+  if (cntL == 0 || cntR == 0) {
+    // rounded centroid beyond an extreme value: the set stays whole
+    emit_leaf_warp<T, D>(P, S, perm, gb, b, e, np, M, s, lane);
+    if (lane == 0) {
+      atomicAdd(&st[kStLeaves], 1ull);
+      atomicAdd(&st[kStDegenerate], 1ull);
+      atomicAdd(&st[kStDepth], (unsigned long long)it.depth * (e - b));
+    }
+    return;
+  }
+  if (lane == 0) {
+    atomicAdd(&st[kStSplits], 1ull);
+    Item ch[2] = {{(uint16_t)b, (uint16_t)(b + cntL), (uint8_t)np, (uint8_t)(it.depth + 1), 0},
+                  {(uint16_t)(b + cntL), (uint16_t)e, (uint8_t)np, (uint8_t)(it.depth + 1), 0}};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int n = ch[h].e - ch[h].b;
+      if (n == 1) {
+        P.perm_final[gb + ch[h].b] = orig_index(perm, gb, S.id[np][ch[h].b]);
+        P.head[gb + ch[h].b] = kHeadSingle;
+        atomicAdd(&st[kStLeaves], 1ull);
+        atomicAdd(&st[kStDepth], (unsigned long long)ch[h].depth);
+      } else if (n <= kSmall) {
+        small[atomicAdd(n_small, 1)] = ch[h];
+      } else {
+        int slot = atomicAdd(n_nxt, 1);
+        if (slot < max_nxt)
+          nxt[slot] = ch[h];
+        else
+          set_error(P.err, kErrInternal);
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- phase B
+
+template <typename T, int D>
+__device__ void thread_finish(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
+                              int64_t gb, Item root, unsigned long long *cnt) {
+  Item stk[kSmall + 2];
+  int sp = 0;
+  stk[sp++] = root;
+  while (sp > 0) {
+    Item it = stk[--sp];
+    const int b = it.b, e = it.e, par = it.par;
+    if (e - b == 1) {
+      P.perm_final[gb + b] = orig_index(perm, gb, S.id[par][b]);
+      P.head[gb + b] = kHeadSingle;
+      cnt[0] += 1;
+      cnt[1] += it.depth;
+      continue;
+    }
+    T s[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) s[l] = S.col(par, l)[b];
+    Moments<T, D> M;
+    M.zero();
+    for (int i = b; i < e; ++i) {
+      T q[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) q[l] = S.col(par, l)[i];
+      M.add(S.col(par, D)[i], q, s);
+    }
+    Cut c = Decider<T, D>::run(P, M, s);
+    if (c.leaf) {
+      emit_leaf_thread<T, D>(P, S, perm, gb, b, e, par, M, s);
+      cnt[0] += 1;
+      cnt[1] += (unsigned long long)it.depth * (e - b);
+      continue;
+    }
+    const int np = par ^ 1;
+    const T *qk = S.col(par, c.k);
+    int cntL = 0, cntR = 0;
+    for (int i = b; i < e; ++i) {
+      bool lft = Decider<T, D>::left(qk[i], c);
+      int dst = lft ? (b + cntL++) : (e - 1 - cntR++);
+#pragma unroll
+      for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
+      S.id[np][dst] = S.id[par][i];
+    }
+    if (cntL == 0 || cntR == 0) {
+      emit_leaf_thread<T, D>(P, S, perm, gb, b, e, np, M, s);
+      cnt[0] += 1;
+      cnt[1] += (unsigned long long)it.depth * (e - b);
+      cnt[3] += 1;
+      continue;
+    }
+    cnt[2] += 1;
+    if (sp + 2 > kSmall + 2) {
+      set_error(P.err, kErrInternal);
+      return;
+    }
+    stk[sp++] = Item{(uint16_t)(b + cntL), (uint16_t)e, (uint8_t)np, (uint8_t)(it.depth + 1), 0};
+    stk[sp++] = Item{(uint16_t)b, (uint16_t)(b + cntL), (uint8_t)np, (uint8_t)(it.depth + 1), 0};
+  }
+}
+
+// ------------------------------------------------------------ unit kernel
+
+// mode 0: units are cells (big cells skipped); mode 1: units are pieces.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) unit_kernel(Problem P, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ctr[4];  // n_cur, n_nxt, n_small, small_next
+  __shared__ int s_unit;
+  __shared__ unsigned long long s_st[kStCount];
+
+  const int cap = P.cap;
+  Tile<T, D> S;
+  S.base = reinterpret_cast<T *>(smem_raw);
+  S.cap = cap;
+  S.id[0] = reinterpret_cast<uint16_t *>(S.base + (size_t)2 * (D + 1) * cap);
+  S.id[1] = S.id[0] + cap;
+  const int max_big = cap / kSmall + 2;
+  Item *lists = reinterpret_cast<Item *>(S.id[1] + cap);
+  Item *cur = lists, *nxt = lists + max_big;
+  Item *small = lists + 2 * max_big;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid < kStCount) s_st[tid] = 0ull;
+  const int n_units = mode == 0 ? P.n_cells : *P.piece_count;
+  const int32_t *perm = (mode == 0 && *P.unsorted == 0) ? nullptr : P.perm;
+  unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};  // leaves, depth, splits, degenerate
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_unit = atomicAdd(P.unit_next + mode, 1);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= n_units) break;
+    int64_t gb;
+    int n, depth0 = 0;
+    if (mode == 0) {
+      gb = P.cell_begin[u];
+      n = P.cell_begin[u + 1] - (int)gb;
+      if (n == 0) continue;
+      if (n <= P.n_min || n == 1) {
+        for (int i = tid; i < n; i += blockDim.x) {
+          P.perm_final[gb + i] = orig_index(perm, gb, i);
+          P.head[gb + i] = kHeadSingle;
+        }
+        if (tid == 0) s_st[kStCellsPass] += 1;
+        continue;
+      }
+      if (n > cap) continue;  // cut first by big_kernel
+      if (tid == 0) s_st[kStCellsMerged] += 1;
+    } else {
+      int4 pc = P.pieces[u];
+      gb = pc.x;
+      n = pc.y - pc.x;
+      depth0 = pc.z;
+    }
+    // stage the unit in shared memory (validating what is read)
+    bool bad = false;
+    for (int i = tid; i < n; i += blockDim.x) {
+      int src = orig_index(perm, gb, i);
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        T x = StoreOf<T>::load(P.q[l], src);
+        bad |= !finite_val(x);
+        S.col(0, l)[i] = x;
+      }
+      T w = StoreOf<T>::load(P.w, src);
+      bad |= !(w > T(0)) || !finite_val(w);
+      S.col(0, D)[i] = w;
+      S.id[0][i] = (uint16_t)i;
+    }
+    if (bad) set_error(P.err, kErrInput);
+    if (tid == 0) {
+      Item root{0, (uint16_t)n, 0, (uint8_t)depth0, 0};
+      s_ctr[0] = 0;
+      s_ctr[1] = 0;
+      s_ctr[2] = 0;
+      s_ctr[3] = 0;
+      if (n <= kSmall) {
+        small[0] = root;
+        s_ctr[2] = 1;
+      } else {
+        cur[0] = root;
+        s_ctr[0] = 1;
+      }
+    }
+    __syncthreads();
+    // phase A: one warp per large subset, level by level
+    for (;;) {
+      const int ncur = s_ctr[0];
+      if (ncur == 0) break;
+      for (int k = warp; k < ncur; k += nwarps)
+        warp_split<T, D>(P, S, perm, gb, cur[k], nxt, &s_ctr[1], max_big, small, &s_ctr[2], s_st,
+                         lane);
+      __syncthreads();
+      if (tid == 0) {
+        s_ctr[0] = min(s_ctr[1], max_big);
+        s_ctr[1] = 0;
+      }
+      Item *t = cur;
+      cur = nxt;
+      nxt = t;
+      __syncthreads();
+    }
+    // phase B: one thread per small subset
+    const int n_small = s_ctr[2];
+    for (;;) {
+      int k = atomicAdd(&s_ctr[3], 1);
+      if (k >= n_small) break;
+      thread_finish<T, D>(P, S, perm, gb, small[k], cnt);
+    }
+  }
+  // flush counters
+  atomicAdd(&s_st[kStLeaves], cnt[0]);
+  atomicAdd(&s_st[kStDepth], cnt[1]);
+  atomicAdd(&s_st[kStSplits], cnt[2]);
+  atomicAdd(&s_st[kStDegenerate], cnt[3]);
+  __syncthreads();
+  if (tid < kStCount && s_st[tid]) atomicAdd(&P.stats[tid], s_st[tid]);
+}
+
+// ------------------------------------------------------------- big kernel
+
+template <typename T, int D>
+struct BlockMoments {
+  Moments<T, D> part[32];
+};
+
+// block-wide moments of perm[b, e) about s; result valid in all threads
+template <typename T, int D>
+__device__ Moments<T, D> block_moments(const Problem &P, const int32_t *perm, int64_t b,
+                                       int64_t e, const T *s, BlockMoments<T, D> &sh,
+                                       bool &bad) {
+  Moments<T, D> M;
+  M.zero();
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    int src = perm[i];
+    T q[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      q[l] = StoreOf<T>::load(P.q[l], src);
+      bad |= !finite_val(q[l]);
+    }
+    T w = StoreOf<T>::load(P.w, src);
+    bad |= !(w > T(0)) || !finite_val(w);
+    M.add(w, q, s);
+  }
+  M.warp_allreduce();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh.part[warp] = M;
+  __syncthreads();
+  Moments<T, D> R = sh.part[0];
+  for (int k = 1; k < nw; ++k) R.merge(sh.part[k]);
+  return R;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(512) big_kernel(Problem P) {
+  constexpr int kStack = 1024;
+  __shared__ int4 stk[kStack];
+  __shared__ int s_sp, s_ticket;
+  __shared__ BlockMoments<T, D> sh;
+  __shared__ int s_wcnt[2][16];
+  __shared__ double s_red[16][D + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const unsigned lt = lanemask_lt();
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_ticket = atomicAdd(P.big_next, 1);
+    __syncthreads();
+    const int t = s_ticket;
+    if (t >= *P.big_count) break;
+    const int c = P.big_list[t];
+    const int64_t gb = P.cell_begin[c], ge = P.cell_begin[c + 1];
+    if (*P.unsorted == 0)
+      for (int64_t i = gb + tid; i < ge; i += blockDim.x) P.perm[i] = (int32_t)i;
+    if (tid == 0) {
+      stk[0] = make_int4((int)gb, (int)ge, 0, 0);
+      s_sp = 1;
+      atomicAdd(&P.stats[kStBig], 1ull);
+      atomicAdd(&P.stats[kStCellsMerged], 1ull);
+    }
+    __syncthreads();
+    while (s_sp > 0) {
+      __syncthreads();
+      const int4 it = stk[s_sp - 1];
+      __syncthreads();
+      if (tid == 0) --s_sp;
+      const int64_t b = it.x, e = it.y;
+      T s[D];
+      const int first = P.perm[b];
+#pragma unroll
+      for (int l = 0; l < D; ++l) s[l] = StoreOf<T>::load(P.q[l], first);
+      bool bad = false;
+      Moments<T, D> M = block_moments<T, D>(P, P.perm, b, e, s, sh, bad);
+      if (bad) set_error(P.err, kErrInput);
+      Cut cut = Decider<T, D>::run(P, M, s);
+      int64_t nL = 0;
+      if (!cut.leaf) {
+        // stable-left / reversed-right partition of perm[b, e) into perm_tmp
+        int64_t cntL = 0, cntR = 0;
+        for (int64_t base = b; base < e; base += blockDim.x) {
+          int64_t i = base + tid;
+          bool valid = i < e;
+          int src = valid ? P.perm[i] : 0;
+          bool lft = valid && Decider<T, D>::left(StoreOf<T>::load(P.q[cut.k], src), cut);
+          unsigned bl = __ballot_sync(0xffffffffu, lft);
+          unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+          __syncthreads();
+          if (lane == 0) {
+            s_wcnt[0][warp] = __popc(bl);
+            s_wcnt[1][warp] = __popc(br);
+          }
+          __syncthreads();
+          int offL = 0, offR = 0, totL = 0, totR = 0;
+          for (int k = 0; k < nw; ++k) {
+            if (k < warp) {
+              offL += s_wcnt[0][k];
+              offR += s_wcnt[1][k];
+            }
+            totL += s_wcnt[0][k];
+            totR += s_wcnt[1][k];
+          }
+          if (valid) {
+            int64_t dst = lft ? (b + cntL + offL + __popc(bl & lt))
+                              : (e - 1 - cntR - offR - __popc(br & lt));
+            P.perm_tmp[dst] = src;
+          }
+          cntL += totL;
+          cntR += totR;
+        }
+        __syncthreads();
+        for (int64_t i = b + tid; i < e; i += blockDim.x) P.perm[i] = P.perm_tmp[i];
+        nL = cntL;
+        if (cntL == 0 || cntR == 0) {
+          cut.leaf = 1;
+          if (tid == 0) atomicAdd(&P.stats[kStDegenerate], 1ull);
+        }
+        __syncthreads();
+      }
+      if (cut.leaf) {
+        for (int64_t i = b + tid; i < e; i += blockDim.x) {
+          P.perm_final[i] = P.perm[i];
+          P.head[i] = (i == b) ? ((e - b == 1) ? kHeadSingle : kHeadMerged) : (uint8_t)0;
+        }
+        // merged W, X, P in FP64
+        double acc[D + 1];
+        if constexpr (sizeof(T) == 8) {
+          acc[0] = M.W.value();
+#pragma unroll
+          for (int l = 0; l < D; ++l) acc[l + 1] = s[l] * acc[0] + M.m1[l].value();
+        } else {
+#pragma unroll
+          for (int l = 0; l <= D; ++l) acc[l] = 0.0;
+          for (int64_t i = b + tid; i < e; i += blockDim.x) {
+            int src = P.perm[i];
+            double w = f2d_exact(StoreOf<T>::load(P.w, src));
+            acc[0] += w;
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+              acc[l + 1] = fma(w, f2d_exact(StoreOf<T>::load(P.q[l], src)), acc[l + 1]);
+          }
+#pragma unroll
+          for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+            for (int l = 0; l <= D; ++l) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], m);
+          __syncthreads();
+          if (lane == 0)
+#pragma unroll
+            for (int l = 0; l <= D; ++l) s_red[warp][l] = acc[l];
+          __syncthreads();
+          if (tid == 0)
+            for (int k = 1; k < nw; ++k)
+#pragma unroll
+              for (int l = 0; l <= D; ++l) acc[l] += s_red[k][l];
+        }
+        if (tid == 0) {
+          if (sizeof(T) == 8) {
+            P.rec_w[b] = M.W.value();
+#pragma unroll
+            for (int l = 0; l < D; ++l)
+              P.rec_c[l * P.stride + b] = (double)s[l] + M.m1[l].value() / M.W.value();
+          } else {
+            P.rec_w[b] = acc[0];
+#pragma unroll
+            for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + b] = acc[l + 1] / acc[0];
+          }
+          atomicAdd(&P.stats[kStLeaves], 1ull);
+          atomicAdd(&P.stats[kStDepth], (unsigned long long)it.z * (e - b));
+        }
+        __syncthreads();
+        continue;
+      }
+      if (tid == 0) {
+        atomicAdd(&P.stats[kStSplits], 1ull);
+        int4 ch[2] = {make_int4((int)b, (int)(b + nL), it.z + 1, 0),
+                      make_int4((int)(b + nL), (int)e, it.z + 1, 0)};
+        for (int h = 1; h >= 0; --h) {
+          int n = ch[h].y - ch[h].x;
+          if (n > P.cap) {
+            if (s_sp < kStack)
+              stk[s_sp++] = ch[h];
+            else
+              set_error(P.err, kErrInternal);
+          } else {
+            int slot = atomicAdd(P.piece_count, 1);
+            if (slot < P.max_pieces)
+              P.pieces[slot] = ch[h];
+            else
+              set_error(P.err, kErrInternal);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launch
+
+template <typename T, int D>
+static cudaError_t launch_units_t(const Problem &P, int mode, int grid, cudaStream_t st) {
+  size_t smem = unit_smem_bytes<T, D>(P.cap);
+  cudaError_t e = cudaFuncSetAttribute(unit_kernel<T, D>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  unit_kernel<T, D><<<grid, 256, smem, st>>>(P, mode);
+  return cudaGetLastError();
+}
+
+template <typename T, int D>
+static cudaError_t launch_big_t(const Problem &P, int grid, cudaStream_t st) {
+  big_kernel<T, D><<<grid, 512, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static size_t smem_t(int D, int cap) {
+  switch (D) {
+    case 2: return unit_smem_bytes<T, 2>(cap);
+    case 3: return unit_smem_bytes<T, 3>(cap);
+    case 4: return unit_smem_bytes<T, 4>(cap);
+    case 5: return unit_smem_bytes<T, 5>(cap);
+    default: return unit_smem_bytes<T, 6>(cap);
+  }
+}
+
+size_t unit_smem(int mixed, int D, int cap) {
+  return mixed ? smem_t<float>(D, cap) : smem_t<double>(D, cap);
+}
+
+#define PMA_DISPATCH_D(FN, T, ...)                        \
+  switch (P.D) {                                          \
+    case 2: return FN<T, 2>(__VA_ARGS__);                 \
+    case 3: return FN<T, 3>(__VA_ARGS__);                 \
+    case 4: return FN<T, 4>(__VA_ARGS__);                 \
+    case 5: return FN<T, 5>(__VA_ARGS__);                 \
+    case 6: return FN<T, 6>(__VA_ARGS__);                 \
+    default: return cudaErrorInvalidValue;                \
+  }
+
+cudaError_t launch_units(const Problem &P, int mixed, int mode, int grid, cudaStream_t st) {
+  if (mixed) {
+    PMA_DISPATCH_D(launch_units_t, float, P, mode, grid, st)
+  } else {
+    PMA_DISPATCH_D(launch_units_t, double, P, mode, grid, st)
+  }
+}
+
+cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st) {
+  if (mixed) {
+    PMA_DISPATCH_D(launch_big_t, float, P, grid, st)
+  } else {
+    PMA_DISPATCH_D(launch_big_t, double, P, grid, st)
+  }
+}
+
+}  // namespace pma

@@ -1,0 +1,220 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_00636_gb300 import binding, synth
+
+from parity import compare, conservation, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(p, **kw):
+    return oracle.merge_particles(p, threads=8, **kw)
+
+
+# ------------------------------------------------------------ FP64 parity
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.counter_beams(),
+    lambda: synth.two_stream(cells=96),
+    lambda: synth.shower(grid=(24, 24)),
+    lambda: synth.random_cell(np.random.default_rng(1), 777, 2, 3, weights="lognormal"),
+], ids=["counter_beams", "two_stream_96", "shower_24x24", "one_cell_777"])
+def test_fp64_matches_oracle(make):
+    p = make()
+    g = run_gpu(p, "fp64")
+    r = _oracle(p)
+    rep = compare(p, g, r)
+    assert g["count_dev"] == g["count"]
+    conservation(p, g)
+    st = g["stats"]
+    assert st["n_out"] == g["count"]
+    assert st["depth_sum"] == r.stats["depth_sum"] or rep["flagged"]
+
+
+def test_fp64_two_stream_full_size():
+    # the full 4096-cell two-stream workload (4.1M particles)
+    p = synth.two_stream()
+    g = run_gpu(p, "fp64")
+    r = _oracle(p)
+    rep = compare(p, g, r)
+    conservation(p, g)
+    assert rep["differing"] <= rep["flagged"]
+
+
+@pytest.mark.parametrize("sizes", [[32], [33], [1, 2, 3], [31, 32, 33, 64, 65, 129]])
+def test_fp64_subset_size_boundaries(sizes):
+    # unit sizes at the warp / thread hand-over and single particles
+    rng = np.random.default_rng(sum(sizes))
+    parts = []
+    for c, m in enumerate(sizes):
+        q = synth.random_cell(rng, m, 1, 3, weights="lognormal")
+        q.cell[:] = c
+        q.pos[0] += c
+        parts.append(q)
+    p = synth.Particles("sizes", 1, 3, len(sizes), (1.0, 1.0, 1.0), 0.05, 0.05, 0,
+                        np.concatenate([q.cell for q in parts]),
+                        np.concatenate([q.pos for q in parts], axis=1),
+                        np.concatenate([q.mom for q in parts], axis=1),
+                        np.concatenate([q.w for q in parts]))
+    g = run_gpu(p, "fp64")
+    compare(p, g, _oracle(p))
+    conservation(p, g)
+
+
+def test_fp64_big_cells_take_the_global_path():
+    # cells above the shared-memory capacity are cut in global memory first
+    rng = np.random.default_rng(9)
+    sizes = [6000, 40, 9000, 2500, 1]
+    parts = []
+    for c, m in enumerate(sizes):
+        q = synth.random_cell(rng, m, 2, 3, weights="lognormal", drift=(0.5, 0.1, -0.2))
+        q.cell[:] = c
+        parts.append(q)
+    p = synth.Particles("big", 2, 3, len(sizes), (1.0, 1.0, 1.0), 0.2, 0.1, 0,
+                        np.concatenate([q.cell for q in parts]),
+                        np.concatenate([q.pos for q in parts], axis=1),
+                        np.concatenate([q.mom for q in parts], axis=1),
+                        np.concatenate([q.w for q in parts]))
+    g = run_gpu(p, "fp64")
+    assert g["stats"]["big_cells"] >= 2
+    compare(p, g, _oracle(p))
+    conservation(p, g)
+
+
+def test_fp64_shuffled_input():
+    p = synth.two_stream(cells=40).shuffled(3)
+    g = run_gpu(p, "fp64")
+    assert g["stats"]["sorted_input"] == 0
+    compare(p, g, _oracle(p))
+    conservation(p, g)
+
+
+def test_fp64_n_min_passthrough():
+    p = synth.counter_beams(cells=8)
+    g = run_gpu(p, "fp64", n_min=200)
+    assert g["count"] == p.n
+    r = _oracle(p, n_min=200)
+    compare(p, g, r)
+    np.testing.assert_array_equal(g["w"], r.w)
+    np.testing.assert_array_equal(g["mom"], r.mom)
+
+
+def test_fp64_identical_particles_and_zero_tolerance():
+    m = 50
+    p = synth.Particles("same", 1, 3, 2, (1.0, 1.0, 1.0), 0.0, 0.0, 0,
+                        np.repeat(np.arange(2, dtype=np.int32), m),
+                        np.full((1, 2 * m), 0.25), np.full((3, 2 * m), 0.5),
+                        np.linspace(0.5, 1.5, 2 * m))
+    p.pos[0, m:] += 1.0
+    g = run_gpu(p, "fp64")
+    # identical values never split; rounding of the centroid may leave a
+    # degenerate cut, which ends the recursion as well
+    assert g["count"] == 2
+    conservation(p, g)
+
+
+def test_empty_input():
+    p = synth.counter_beams(cells=4)
+    e = synth.Particles("empty", 1, 3, 4, (1.0, 1.0, 1.0), 0.1, 0.1, 0,
+                        p.cell[:0], p.pos[:, :0], p.mom[:, :0], p.w[:0])
+    g = run_gpu(e, "fp64", capacity=16)
+    assert g["count"] == 0 and g["count_dev"] == 0
+
+
+# ----------------------------------------------------------- mixed path
+
+@pytest.mark.parametrize("make", [
+    lambda: synth.two_stream_f32(cells=128),
+    lambda: synth.shower(grid=(24, 24)).astype(np.float32),
+    lambda: synth.hot_6d(grid=(10, 10, 10), hot_count=3000, hot_frac=0.005),
+], ids=["two_stream_f32", "shower_f32", "hot_6d_small"])
+def test_mixed_against_oracle_on_rounded_inputs(make):
+    p = make()
+    g = run_gpu(p, "mixed")
+    r = _oracle(p)  # oracle on the float32 values, upcast exactly
+    # membership: the mixed sums may flip decisions within ~1e-6 of a tie
+    from parity import local_index
+    gi = local_index(g["index"], p.cell, g["cell"], p.n_cells)
+    oi = local_index(r.index, p.cell, r.cell, p.n_cells)
+    diff_cells = np.unique(p.cell[gi != oi])
+    frac = diff_cells.size / max(1, np.unique(p.cell).size)
+    assert frac <= 0.01, "too many cells differ: %d" % diff_cells.size
+    # conservation of W and W P per cell to 1e-12 (merged W, P are FP64 sums)
+    conservation(p, g)
+
+
+# --------------------------------------------------------- API behaviour
+
+def test_async_merge_then_sync_and_host_variant():
+    import torch
+    p = synth.two_stream(cells=16)
+    m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, "fp64")
+    dev = torch.device("cuda", 0)
+    cells = torch.from_numpy(p.cell).to(dev)
+    pos = [torch.from_numpy(p.pos[0].copy()).to(dev)]
+    mom = [torch.from_numpy(p.mom[a].copy()).to(dev) for a in range(3)]
+    w = torch.from_numpy(p.w).to(dev)
+    M0, out0 = m.merge(cells, pos, mom, w, p.tol_x, p.tol_p)
+    _, out1 = m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, sync=False)
+    m.sync()
+    assert int(out1.count_dev.item()) == M0
+    assert torch.equal(out0.index, out1.index)
+    # host-buffer variant
+    N = p.n
+    hc = np.empty(N, np.int32)
+    hp = [np.empty(N) for _ in range(1)]
+    hm = [np.empty(N) for _ in range(3)]
+    hw = np.empty(N)
+    hi = np.empty(N, np.int32)
+    o = binding.pma_output()
+    o.cell = hc.ctypes.data
+    o.pos[0] = hp[0].ctypes.data
+    for a in range(3):
+        o.mom[a] = hm[a].ctypes.data
+    o.w = hw.ctypes.data
+    o.index = hi.ctypes.data
+    pc = [np.ascontiguousarray(p.pos[0])]
+    mc = [np.ascontiguousarray(p.mom[a]) for a in range(3)]
+    M = binding.pma_merge_host(m.handle, N, p.cell.ctypes.data, [x.ctypes.data for x in pc],
+                               [x.ctypes.data for x in mc], p.w.ctypes.data, p.tol_x, p.tol_p, o)
+    assert M == M0
+    np.testing.assert_array_equal(hi, out0.index.cpu().numpy())
+    np.testing.assert_array_equal(hw[:M], out0.w[:M].cpu().numpy())
+    m.close()
+
+
+@pytest.mark.parametrize("bad", ["cell", "weight", "nan"])
+def test_bad_particle_data_is_reported(bad):
+    p = synth.counter_beams(cells=4)
+    if bad == "cell":
+        p.cell[5] = 99
+    elif bad == "weight":
+        p.w[7] = -1.0
+    else:
+        p.mom[1, 9] = np.nan
+    with pytest.raises(binding.PmaError) as ei:
+        run_gpu(p, "fp64")
+    assert ei.value.code == binding.PMA_ERR_INPUT
+
+
+def test_capacity_and_tolerance_checks():
+    import torch
+    p = synth.counter_beams(cells=2)
+    m = binding.Merger(1, 3, 2, 100, precision="fp64")
+    dev = torch.device("cuda", 0)
+    cells = torch.from_numpy(p.cell).to(dev)
+    pos = [torch.from_numpy(p.pos[0].copy()).to(dev)]
+    mom = [torch.from_numpy(p.mom[a].copy()).to(dev) for a in range(3)]
+    w = torch.from_numpy(p.w).to(dev)
+    with pytest.raises(binding.PmaError) as ei:
+        m.merge(cells, pos, mom, w, 0.1, 0.1)
+    assert ei.value.code == binding.PMA_ERR_CAPACITY
+    m.close()
+    m = binding.Merger(1, 3, 2, p.n, precision="fp64")
+    with pytest.raises(binding.PmaError) as ei:
+        m.merge(cells, pos, mom, w, -0.1, 0.1)
+    assert ei.value.code == binding.PMA_ERR_INVALID_ARG
+    m.close()
