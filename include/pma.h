@@ -158,6 +158,42 @@ int pma_get_stats(const pma_handle *h, pma_stats *out);
 int pma_set_timing(pma_handle *h, int enable);
 int pma_get_timing(const pma_handle *h, float *ms, int n);
 
+/*
+ * Allocation-free merge.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory, for example a
+ * PIC code whose device memory is owned by its own pool allocator, or a
+ * host thread that must not trigger the implicit device synchronisation
+ * that cudaMalloc/cudaFree can cause in the middle of a time step.  It
+ * needs no handle: its scratch is a fixed array inside the library (about
+ * 4.5 MB, held by every GPU that loads the library until the process
+ * exits), and the caller passes only inputs and outputs.
+ *   cfg          dx, dp, cell_size, n_cells, n_min and precision as for
+ *                pma_create (capacity and flags are ignored)
+ *   n, cells, pos, mom, weights, tol_x, tol_p   as for pma_merge; the cell
+ *                ids must be non-decreasing (particles grouped by cell)
+ *   out          caller-owned device outputs as for pma_merge
+ *   count_host   host int64 receiving M, or NULL
+ * Limits: n <= PMA_NOALLOC_MAX_N and n_cells <= PMA_NOALLOC_MAX_CELLS,
+ * else PMA_ERR_CAPACITY before any device work; every cell with more than
+ * n_min particles must fit one CTA's shared memory (over 2,000 particles
+ * for D <= 4), else the call returns PMA_ERR_CAPACITY after the device work.
+ * Unsorted or out-of-range cell ids and bad particle values return
+ * PMA_ERR_INPUT.
+ * The call waits for `stream` and returns the device status.  The first
+ * call on each device looks up the scratch array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array, which keeps the last
+ * call's contents (the part that must start at zero is cleared by every
+ * call): calls that overlap on the GPU, from several streams or host
+ * threads, race and give wrong results.
+ */
+#define PMA_NOALLOC_MAX_N 65536
+#define PMA_NOALLOC_MAX_CELLS 65536
+int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t *cells,
+                      const void *const *pos, const void *const *mom,
+                      const void *weights, double tol_x, double tol_p,
+                      const pma_output *out, int64_t *count_host, void *stream);
+
 /* Release the handle and its device memory (NULL is accepted). */
 int pma_destroy(pma_handle *h);
 

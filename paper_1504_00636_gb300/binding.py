@@ -29,8 +29,10 @@ PMA_MIXED = 1
 PMA_FLAG_NO_INDEX = 1
 
 SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
-           "pma_set_timing", "pma_get_timing", "pma_destroy", "pma_error_string",
-           "pma_last_error")
+           "pma_set_timing", "pma_get_timing", "pma_merge_noalloc", "pma_destroy",
+           "pma_error_string", "pma_last_error")
+PMA_NOALLOC_MAX_N = 65536
+PMA_NOALLOC_MAX_CELLS = 65536
 PMA_N_STAGES = 6
 STAGES = ("binning", "big_cells", "cells", "pieces", "emit", "total")
 
@@ -96,6 +98,8 @@ def load(build_if_missing: bool = True):
             lib.pma_set_timing.restype = ctypes.c_int
             lib.pma_get_timing.argtypes = [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
             lib.pma_get_timing.restype = ctypes.c_int
+            lib.pma_merge_noalloc.argtypes = [ctypes.POINTER(pma_config)] + args[1:]
+            lib.pma_merge_noalloc.restype = ctypes.c_int
             lib.pma_destroy.argtypes = [P]
             lib.pma_destroy.restype = ctypes.c_int
             lib.pma_error_string.argtypes = [ctypes.c_int]
@@ -153,6 +157,22 @@ def pma_merge_host(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_o
     rc = load().pma_merge_host(handle, n, cells, _ptrs(pos), _ptrs(mom), weights, tol_x, tol_p,
                                ctypes.byref(out), ctypes.byref(cnt), stream)
     _check(rc, handle)
+    return cnt.value
+
+
+def pma_merge_noalloc(cfg: pma_config, n, cells, pos, mom, weights, tol_x, tol_p,
+                      out: pma_output, stream=0):
+    """Raw call of the allocation-free entry point (device pointers as ints).
+
+    For callers that must not allocate device memory: no handle, scratch in
+    a fixed array inside the library, n <= PMA_NOALLOC_MAX_N particles
+    grouped by cell, n_cells <= PMA_NOALLOC_MAX_CELLS.  Waits for `stream`.
+    """
+    cnt = ctypes.c_int64(-1)
+    rc = load().pma_merge_noalloc(ctypes.byref(cfg), n, cells, _ptrs(pos), _ptrs(mom), weights,
+                                  tol_x, tol_p, ctypes.byref(out), ctypes.byref(cnt), stream)
+    if rc != PMA_OK:
+        raise PmaError(rc, "pma_merge_noalloc")
     return cnt.value
 
 

@@ -14,6 +14,11 @@
 // big_kernel: cells larger than the shared-memory capacity are cut by a whole
 // CTA in global memory (on the permutation array only) until every piece
 // fits; the pieces then go through unit_kernel.
+#include <cstddef>
+#include <mutex>
+
+#include "lookback.cuh"
+#include "pma.h"
 #include "pma_device.cuh"
 #include "pma_launch.h"
 
@@ -704,3 +709,373 @@ cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st) {
 }
 
 }  // namespace pma
+
+// ============================================================================
+// Allocation-free variant (pma_merge_noalloc in include/pma.h).
+//
+// For callers that must not allocate device memory, the per-cell kernel
+// above is repeated here with its scratch (look-back words, final
+// permutation, head bytes, centroid records) in one file-scope device array
+// of fixed size, and the Step 7 emission fused into the same kernel: each
+// CTA takes cells in ascending order, partitions one in shared memory,
+// counts its final sets, gets the number of sets before it by decoupled
+// look-back over cells, and writes its merged particles.  Input must be
+// grouped by cell (non-decreasing ids); cell ranges are found by binary
+// search, so no binning workspace is needed.
+// ============================================================================
+
+namespace pma {
+
+struct NoAllocScratch {
+  // must be zero when a call starts
+  unsigned long long status[PMA_NOALLOC_MAX_CELLS];
+  int32_t ticket;
+  unsigned err;
+  int64_t count;
+  unsigned long long stats[kStCount];
+  // written before being read within a call
+  int32_t perm_final[PMA_NOALLOC_MAX_N];
+  double rec_w[PMA_NOALLOC_MAX_N];
+  double rec_c[kMaxD * PMA_NOALLOC_MAX_N];
+  uint8_t head[PMA_NOALLOC_MAX_N];
+};
+constexpr size_t kNoAllocZeroBytes = offsetof(NoAllocScratch, perm_final);
+constexpr unsigned kErrCellTooBig = 8u;
+
+// Every device that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+struct NoAllocOut {
+  int32_t *cell;
+  void *pos[3];
+  double *mom[3];
+  double *w;
+  int32_t *index;
+  int64_t *count_dev;
+};
+
+__device__ __forceinline__ int lower_bound_cell(const int32_t *cells, int n, int c) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cells[mid] < c)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) noalloc_kernel(Problem P, NoAllocScratch *Sc, int n,
+                                                      NoAllocOut o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ctr[4];
+  __shared__ int s_cell, s_b, s_e;
+  __shared__ int s_warp[32];
+  __shared__ long long s_base;
+  __shared__ unsigned long long s_st[kStCount];
+
+  const int cap = P.cap;
+  Tile<T, D> S;
+  S.base = reinterpret_cast<T *>(smem_raw);
+  S.cap = cap;
+  S.id[0] = reinterpret_cast<uint16_t *>(S.base + (size_t)2 * (D + 1) * cap);
+  S.id[1] = S.id[0] + cap;
+  const int max_big = cap / kSmall + 2;
+  Item *lists = reinterpret_cast<Item *>(S.id[1] + cap);
+  Item *cur = lists, *nxt = lists + max_big;
+  Item *small = lists + 2 * max_big;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid < kStCount) s_st[tid] = 0ull;
+  unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
+
+  // ids in range and non-decreasing (the binary search relies on it)
+  for (int i = blockIdx.x * blockDim.x + tid; i < n; i += gridDim.x * blockDim.x) {
+    int c = P.cells[i];
+    if (c < 0 || c >= P.n_cells || (i > 0 && P.cells[i - 1] > c)) atomicOr(&Sc->err, kErrInput);
+  }
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      int c = atomicAdd(&Sc->ticket, 1);
+      s_cell = c;
+      if (c < P.n_cells) {
+        s_b = lower_bound_cell(P.cells, n, c);
+        s_e = lower_bound_cell(P.cells, n, c + 1);
+        if (s_e < s_b) s_e = s_b;
+      }
+    }
+    __syncthreads();
+    const int c = s_cell;
+    if (c >= P.n_cells) break;
+    const int64_t gb = s_b;
+    const int m = s_e - s_b;
+    const bool pass = m > 0 && (m <= P.n_min || m == 1 || m > cap);
+    if (m > cap && m > P.n_min && m > 1 && tid == 0) atomicOr(&Sc->err, kErrCellTooBig);
+    if (pass) {
+      for (int i = tid; i < m; i += blockDim.x) {
+        P.perm_final[gb + i] = (int)(gb + i);
+        P.head[gb + i] = kHeadSingle;
+      }
+    } else if (m > 0) {
+      bool bad = false;
+      for (int i = tid; i < m; i += blockDim.x) {
+        const int src = (int)(gb + i);
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          T x = StoreOf<T>::load(P.q[l], src);
+          bad |= !finite_val(x);
+          S.col(0, l)[i] = x;
+        }
+        T w = StoreOf<T>::load(P.w, src);
+        bad |= !(w > T(0)) || !finite_val(w);
+        S.col(0, D)[i] = w;
+        S.id[0][i] = (uint16_t)i;
+      }
+      if (bad) atomicOr(&Sc->err, kErrInput);
+      if (tid == 0) {
+        Item root{0, (uint16_t)m, 0, 0, 0};
+        s_ctr[0] = s_ctr[1] = s_ctr[2] = s_ctr[3] = 0;
+        if (m <= kSmall) {
+          small[0] = root;
+          s_ctr[2] = 1;
+        } else {
+          cur[0] = root;
+          s_ctr[0] = 1;
+        }
+      }
+      __syncthreads();
+      for (;;) {
+        const int ncur = s_ctr[0];
+        if (ncur == 0) break;
+        for (int k = warp; k < ncur; k += nwarps)
+          warp_split<T, D>(P, S, nullptr, gb, cur[k], nxt, &s_ctr[1], max_big, small, &s_ctr[2],
+                           s_st, lane);
+        __syncthreads();
+        if (tid == 0) {
+          s_ctr[0] = min(s_ctr[1], max_big);
+          s_ctr[1] = 0;
+        }
+        Item *t = cur;
+        cur = nxt;
+        nxt = t;
+        __syncthreads();
+      }
+      const int n_small = s_ctr[2];
+      for (;;) {
+        int k = atomicAdd(&s_ctr[3], 1);
+        if (k >= n_small) break;
+        thread_finish<T, D>(P, S, nullptr, gb, small[k], cnt);
+      }
+    }
+    __syncthreads();
+    // Step 7 for this cell: count its sets, prefix over cells, write outputs
+    const int per = (m + blockDim.x - 1) / blockDim.x;
+    const int p0 = min(m, tid * per), p1 = min(m, p0 + per);
+    int heads = 0;
+    for (int p = p0; p < p1; ++p) heads += P.head[gb + p] != 0;
+    int total;
+    const int ex = block_exclusive_scan(heads, s_warp, &total);
+    if (tid == 0) {
+      s_base = tile_exclusive_prefix(Sc->status, c, total, &Sc->err);
+      if (c == P.n_cells - 1) {
+        Sc->count = s_base + total;
+        if (o.count_dev) *o.count_dev = s_base + total;
+      }
+    }
+    __syncthreads();
+    long long run = s_base + ex;
+    for (int p = p0; p < p1; ++p) {
+      const int64_t gp = gb + p;
+      const uint8_t h = P.head[gp];
+      if (h) ++run;
+      const long long slot = run - 1;
+      const int orig = P.perm_final[gp];
+      if (slot < 0 || (unsigned)orig >= (unsigned)n) {
+        atomicOr(&Sc->err, kErrInternal);
+        continue;
+      }
+      if (o.index) o.index[orig] = (int32_t)slot;
+      if (!h) continue;
+      o.cell[slot] = c;
+      if (h == kHeadSingle) {
+        for (int l = 0; l < P.dx; ++l)
+          static_cast<T *>(o.pos[l])[slot] = StoreOf<T>::load(P.q[l], orig);
+        for (int l = 0; l < P.D - P.dx; ++l) {
+          T x = StoreOf<T>::load(P.q[P.dx + l], orig);
+          o.mom[l][slot] = sizeof(T) == 4 ? f2d_exact((float)x) : (double)x;
+        }
+        T w = StoreOf<T>::load(P.w, orig);
+        if (!(w > T(0)) || !finite_val(w)) atomicOr(&Sc->err, kErrInput);
+        o.w[slot] = sizeof(T) == 4 ? f2d_exact((float)w) : (double)w;
+      } else {
+        o.w[slot] = P.rec_w[gp];
+        for (int l = 0; l < P.dx; ++l)
+          static_cast<T *>(o.pos[l])[slot] = (T)P.rec_c[l * P.stride + gp];
+        for (int l = 0; l < P.D - P.dx; ++l) o.mom[l][slot] = P.rec_c[(P.dx + l) * P.stride + gp];
+      }
+    }
+  }
+  atomicAdd(&s_st[kStLeaves], cnt[0]);
+  atomicAdd(&s_st[kStSplits], cnt[2]);
+  __syncthreads();
+  if (tid < kStCount && s_st[tid]) atomicAdd(&Sc->stats[tid], s_st[tid]);
+}
+
+template <typename T, int D>
+static cudaError_t launch_noalloc_t(const Problem &P, NoAllocScratch *Sc, int n,
+                                    const NoAllocOut &o, int grid, cudaStream_t st) {
+  size_t smem = unit_smem_bytes<T, D>(P.cap);
+  cudaError_t e = cudaFuncSetAttribute(noalloc_kernel<T, D>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  noalloc_kernel<T, D><<<grid, 256, smem, st>>>(P, Sc, n, o);
+  return cudaGetLastError();
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices];  // device address of the scratch, per device
+int g_noalloc_sms[kMaxDevices];
+int g_noalloc_smem[kMaxDevices];
+}  // namespace
+
+}  // namespace pma
+
+extern "C" int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t *cells,
+                                 const void *const *pos, const void *const *mom,
+                                 const void *weights, double tol_x, double tol_p,
+                                 const pma_output *out, int64_t *count_host, void *stream) {
+  using namespace pma;
+  if (!cfg || !out) return PMA_ERR_INVALID_ARG;
+  if (cfg->dx < 1 || cfg->dx > 3 || cfg->dp < 1 || cfg->dp > 3 || cfg->n_min < 0 ||
+      cfg->n_cells < 1 || (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED))
+    return PMA_ERR_INVALID_ARG;
+  for (int a = 0; a < cfg->dx; ++a)
+    if (!(cfg->cell_size[a] > 0.0) || !isfinite(cfg->cell_size[a])) return PMA_ERR_INVALID_ARG;
+  if (!(tol_x >= 0.0) || !(tol_p >= 0.0) || !isfinite(tol_x) || !isfinite(tol_p))
+    return PMA_ERR_INVALID_ARG;
+  if (n < 0) return PMA_ERR_INVALID_ARG;
+  if (n > PMA_NOALLOC_MAX_N || cfg->n_cells > PMA_NOALLOC_MAX_CELLS) return PMA_ERR_CAPACITY;
+  if (n > 0) {
+    if (!cells || !pos || !mom || !weights || !out->cell || !out->w) return PMA_ERR_INVALID_ARG;
+    for (int a = 0; a < cfg->dx; ++a)
+      if (!pos[a] || !out->pos[a]) return PMA_ERR_INVALID_ARG;
+    for (int a = 0; a < cfg->dp; ++a)
+      if (!mom[a] || !out->mom[a]) return PMA_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PMA_ERR_CUDA;
+  // once per device, with that device current: the scratch array's device
+  // address (the symbol itself is a host-side stand-in)
+  void *addr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return PMA_ERR_CUDA;
+      }
+      int sms = 0, smem = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+              cudaSuccess)
+        return PMA_ERR_CUDA;
+      g_noalloc_sms[dev] = sms;
+      g_noalloc_smem[dev] = smem;
+      g_noalloc_addr[dev] = p;
+    }
+    addr = g_noalloc_addr[dev];
+  }
+  NoAllocScratch *Sc = static_cast<NoAllocScratch *>(addr);
+  if (cudaMemsetAsync(Sc, 0, kNoAllocZeroBytes, st) != cudaSuccess) return PMA_ERR_CUDA;
+  if (n == 0) {
+    if (out->count_dev && cudaMemsetAsync(out->count_dev, 0, sizeof(int64_t), st) != cudaSuccess)
+      return PMA_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PMA_ERR_CUDA;
+    if (count_host) *count_host = 0;
+    return PMA_OK;
+  }
+  const int mixed = cfg->precision == PMA_MIXED;
+  const int D = cfg->dx + cfg->dp;
+  int cap = 8192;
+  while (cap > 64 && unit_smem(mixed, D, cap) + 4096 > (size_t)g_noalloc_smem[dev]) cap -= 64;
+
+  Problem P{};
+  P.n_cells = (int32_t)cfg->n_cells;
+  P.dx = cfg->dx;
+  P.D = D;
+  P.n_min = cfg->n_min;
+  P.cap = cap;
+  P.tol2_x = tol_x * tol_x;
+  P.tol2_p = tol_p * tol_p;
+  P.tol2_xf = (float)P.tol2_x;
+  P.tol2_pf = (float)P.tol2_p;
+  for (int a = 0; a < 3; ++a) {
+    double L = a < cfg->dx ? cfg->cell_size[a] : 1.0;
+    P.L2[a] = L * L;
+    P.L2f[a] = (float)P.L2[a];
+  }
+  for (int a = 0; a < cfg->dx; ++a) P.q[a] = pos[a];
+  for (int a = 0; a < cfg->dp; ++a) P.q[cfg->dx + a] = mom[a];
+  P.w = weights;
+  P.cells = cells;
+  P.head = Sc->head;
+  P.perm_final = Sc->perm_final;
+  P.rec_w = Sc->rec_w;
+  P.rec_c = Sc->rec_c;
+  P.stride = PMA_NOALLOC_MAX_N;
+  P.err = &Sc->err;
+  P.stats = Sc->stats;
+  NoAllocOut o{};
+  o.cell = out->cell;
+  for (int a = 0; a < 3; ++a) {
+    o.pos[a] = out->pos[a];
+    o.mom[a] = out->mom[a];
+  }
+  o.w = out->w;
+  o.index = out->index;
+  o.count_dev = out->count_dev;
+  const int grid = (int)std::min<int64_t>(cfg->n_cells, g_noalloc_sms[dev]);
+  cudaError_t e;
+#define PMA_NOALLOC_CASE(TT, DD) e = launch_noalloc_t<TT, DD>(P, Sc, (int)n, o, grid, st)
+  if (mixed) {
+    switch (D) {
+      case 2: PMA_NOALLOC_CASE(float, 2); break;
+      case 3: PMA_NOALLOC_CASE(float, 3); break;
+      case 4: PMA_NOALLOC_CASE(float, 4); break;
+      case 5: PMA_NOALLOC_CASE(float, 5); break;
+      default: PMA_NOALLOC_CASE(float, 6); break;
+    }
+  } else {
+    switch (D) {
+      case 2: PMA_NOALLOC_CASE(double, 2); break;
+      case 3: PMA_NOALLOC_CASE(double, 3); break;
+      case 4: PMA_NOALLOC_CASE(double, 4); break;
+      case 5: PMA_NOALLOC_CASE(double, 5); break;
+      default: PMA_NOALLOC_CASE(double, 6); break;
+    }
+  }
+#undef PMA_NOALLOC_CASE
+  if (e != cudaSuccess) return PMA_ERR_CUDA;
+  struct {
+    int32_t ticket;
+    unsigned err;
+    int64_t count;
+  } st_host{};
+  if (cudaMemcpyAsync(&st_host, &Sc->ticket, sizeof(st_host), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PMA_ERR_CUDA;
+  if (count_host) *count_host = st_host.count;
+  if (st_host.err & kErrInput) return PMA_ERR_INPUT;
+  if (st_host.err & kErrCellTooBig) return PMA_ERR_CAPACITY;
+  if (st_host.err & kErrTimeout) return PMA_ERR_TIMEOUT;
+  if (st_host.err & kErrInternal) return PMA_ERR_INTERNAL;
+  return PMA_OK;
+}
