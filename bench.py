@@ -36,7 +36,7 @@ UNIT = "Mparticles/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 FP32_OPS_PEAK = 152 * 128 * 2.07e9  # FP32 lanes x SMs x max clock (instr/s)
 FP64_OPS_PEAK = 1.25e12 / 2.0       # nominal GB300 FP64 FMA rate (ops/s)
-KERNELS_PER_STEP = 7  # hist, scan, scatter, big, unit(cells), unit(pieces), emit
+KERNELS_PER_STEP = 8  # hist, scan, scatter, big, warp(cells), unit(cells), unit(pieces), emit
 
 
 def load_peaks():
@@ -134,7 +134,7 @@ def bytes_per_particle(p, mixed):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("split.cu", "pma_device.cuh"):
+    for f in ("warp.cu", "split_common.cuh", "pma_device.cuh"):
         with open(os.path.join(ROOT, "paper_1504_00636_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -259,9 +259,9 @@ def time_oracle(p, threads, reps):
 
 
 def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name):
-    """Roofline of the dominant kernel (per-cell partition, unit_kernel)."""
+    """Roofline of the dominant kernel (per-cell partition: warp_kernel)."""
     b_in, _ = bytes_per_particle(p, mixed)
-    t = stage_ms["cells"] * 1e-3
+    t = stage_ms["warp_cells"] * 1e-3
     n = p.n
     # per launch it reads every particle of the cells it owns once and writes
     # the 4-byte final permutation and the head byte of every particle
@@ -271,17 +271,17 @@ def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name):
     hbm = peaks["hbm_gbs"] * 1e9
     alu_peak = FP32_OPS_PEAK if mixed else FP64_OPS_PEAK
     t_hbm, t_alu = bytes_alg / hbm, ops_alg / alu_peak
-    traffic = ncu_traffic("unit_kernel", workload_name, "mixed" if mixed else "fp64")
+    traffic = ncu_traffic("warp_kernel", workload_name, "mixed" if mixed else "fp64")
     if t_hbm >= t_alu:
         ach = bytes_alg / t / 1e9
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                "traffic": traffic, "kernel": "unit_kernel",
+                "traffic": traffic, "kernel": "warp_kernel",
                 "peak_source": peak_kind}
     ach = ops_alg / t / 1e12
     return {"bound": "alu", "achieved": round(ach, 4), "peak": round(alu_peak / 1e12, 3),
             "unit": "Tops/s", "frac": round(ach / (alu_peak / 1e12), 4), "traffic": traffic,
-            "kernel": "unit_kernel",
+            "kernel": "warp_kernel",
             "peak_source": "FP32 lanes x SMs x max clock" if mixed else
             "nominal GB300 FP64 1.25 TFLOP/s / 2"}
 

@@ -150,11 +150,12 @@ int pma_get_stats(const pma_handle *h, pma_stats *out);
  * events on its stream between the stages; pma_get_timing (after the call
  * completed) writes up to n durations in milliseconds, averaged over the
  * calls since timing was enabled (the last 64 of them):
- *   [0] Step 1 binning   [1] big-cell cuts   [2] per-cell partition
- *   [3] big-cell pieces  [4] Step 7 emit     [5] whole call
+ *   [0] Step 1 binning        [1] big-cell cuts (global memory)
+ *   [2] warp-per-cell cells   [3] CTA-per-cell cells   [4] big-cell pieces
+ *   [5] Step 7 emit           [6] whole call
  * and returns PMA_ERR_INVALID_ARG when timing is off or nothing was timed.
  */
-#define PMA_N_STAGES 6
+#define PMA_N_STAGES 7
 int pma_set_timing(pma_handle *h, int enable);
 int pma_get_timing(const pma_handle *h, float *ms, int n);
 

@@ -33,8 +33,8 @@ SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_sta
            "pma_error_string", "pma_last_error")
 PMA_NOALLOC_MAX_N = 65536
 PMA_NOALLOC_MAX_CELLS = 65536
-PMA_N_STAGES = 6
-STAGES = ("binning", "big_cells", "cells", "pieces", "emit", "total")
+PMA_N_STAGES = 7
+STAGES = ("binning", "big_cells", "warp_cells", "block_cells", "pieces", "emit", "total")
 
 
 class pma_config(ctypes.Structure):

@@ -31,6 +31,9 @@ struct Ctl {
   int32_t big_next;
   int32_t piece_count;
   int32_t unit_next[2];
+  int32_t warp_count;
+  int32_t warp_next;
+  int32_t block_count;
   int32_t bin_ticket;
   int32_t emit_ticket;
   int32_t pad;
@@ -62,6 +65,9 @@ struct pma_handle {
   int mixed = 0;
   int cap = 0;
   int unit_grid = 0;
+  int cap_w = 0;
+  int warps_per_cta = 0;
+  int warp_grid = 0;
   int64_t capacity = 0;
   int bin_tiles = 0;
   int emit_tiles_max = 0;
@@ -69,6 +75,7 @@ struct pma_handle {
   // workspace
   int32_t *counts = nullptr, *cell_begin = nullptr, *fill = nullptr;
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
+  int32_t *warp_list = nullptr, *block_list = nullptr;
   uint8_t *head = nullptr;
   double *rec_w = nullptr, *rec_c = nullptr;
   unsigned long long *bin_status = nullptr, *emit_status = nullptr;
@@ -80,7 +87,7 @@ struct pma_handle {
   Staging stage;
   bool timing = false;
   int timed = 0;     // calls recorded since timing was enabled
-  cudaEvent_t ev[kRing][PMA_N_STAGES] = {};
+  cudaEvent_t ev[kRing][PMA_N_STAGES] = {};  // PMA_N_STAGES events per call
   cudaEvent_t *cur_ev = nullptr;
   std::string last_error;
   pma_stats stats{};
@@ -112,7 +119,7 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->rec_w, h->rec_c, h->bin_status, h->emit_status,
-                  h->pieces, h->ctl, h->stage.cells, h->stage.w, h->stage.out_cell,
+                  h->pieces, h->ctl, h->warp_list, h->block_list, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -128,8 +135,8 @@ void free_all(pma_handle *h) {
       if (e) cudaEventDestroy(e);
 }
 
-// event i of the current call: 0 before binning, 1..4 after each stage,
-// 5 after emit (6 events; stage k spans events k..k+1, the call 0..5)
+// event i of the current call: 0 before binning, 1..6 after each stage
+// (stage k spans events k..k+1, the whole call 0..6)
 void mark(pma_handle *h, int i, cudaStream_t st) {
   if (h->timing && h->cur_ev) cudaEventRecord(h->cur_ev[i], st);
 }
@@ -207,6 +214,15 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   while (cap > 64 && unit_smem(h->mixed, h->D, cap) + 4096 > (size_t)smem_optin) cap -= 64;
   h->cap = cap;
   h->unit_grid = h->sms;
+  // warp-per-cell class: cells up to cap_w particles, one warp each
+  const size_t smem_sm = (size_t)smem_optin + 1024;
+  h->cap_w = 1024;
+  h->warps_per_cta = 4;
+  while (h->warps_per_cta > 1 &&
+         (size_t)h->warps_per_cta * warp_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
+    --h->warps_per_cta;
+  const size_t cta_smem = (size_t)h->warps_per_cta * warp_smem(h->mixed, h->D, h->cap_w);
+  h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (cta_smem + 1024)));
   const int64_t N = std::max<int64_t>(cfg->capacity, 1);
   const int64_t C = cfg->n_cells;
   h->bin_tiles = scan_tiles_for(C);
@@ -217,6 +233,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->fill, C) == cudaSuccess && dalloc(&h->perm, N) == cudaSuccess &&
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
+            dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
             dalloc(&h->rec_w, N) == cudaSuccess &&
             dalloc(&h->rec_c, (size_t)N * h->D) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
@@ -290,6 +307,11 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   b.unsorted = &h->ctl->unsorted;
   b.big_list = h->big_list;
   b.big_count = &h->ctl->big_count;
+  b.cap_w = h->cap_w;
+  b.warp_list = h->warp_list;
+  b.warp_count = &h->ctl->warp_count;
+  b.block_list = h->block_list;
+  b.block_count = &h->ctl->block_count;
   b.err = &h->ctl->err;
   b.scan_status = h->bin_status;
   b.scan_ticket = &h->ctl->bin_ticket;
@@ -337,16 +359,25 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.perm_tmp = h->perm_tmp;
   P.max_pieces = h->max_pieces;
   P.unit_next = h->ctl->unit_next;
+  P.cap_w = h->cap_w;
+  P.warp_list = h->warp_list;
+  P.warp_count = &h->ctl->warp_count;
+  P.warp_next = &h->ctl->warp_next;
+  P.block_list = h->block_list;
+  P.block_count = &h->ctl->block_count;
 
   e = launch_big(P, h->mixed, h->sms, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);
+  e = launch_warps(P, h->mixed, h->warps_per_cta, h->warp_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "warp launch (cells)");
+  mark(h, 3, st);
   e = launch_units(P, h->mixed, 0, h->unit_grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (cells)");
-  mark(h, 3, st);
+  mark(h, 4, st);
   e = launch_units(P, h->mixed, 1, h->unit_grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (pieces)");
-  mark(h, 4, st);
+  mark(h, 5, st);
 
   EmitArgs m{};
   m.n = n;
@@ -376,7 +407,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.tiles = tiles;
   e = launch_emit(m, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "emit launch");
-  mark(h, 5, st);
+  mark(h, 6, st);
   if (h->timing) ++h->timed;
   return PMA_OK;
 }
@@ -429,8 +460,8 @@ int pma_set_timing(pma_handle *h, int enable) {
 
 int pma_get_timing(const pma_handle *h, float *ms, int n) {
   if (!h || !ms || h->timed == 0) return PMA_ERR_INVALID_ARG;
-  static const int from[PMA_N_STAGES] = {0, 1, 2, 3, 4, 0};
-  static const int to[PMA_N_STAGES] = {1, 2, 3, 4, 5, 5};
+  static const int from[PMA_N_STAGES] = {0, 1, 2, 3, 4, 5, 0};
+  static const int to[PMA_N_STAGES] = {1, 2, 3, 4, 5, 6, 6};
   const int calls = h->timed < kRing ? h->timed : kRing;
   for (int i = 0; i < n && i < PMA_N_STAGES; ++i) {
     double sum = 0.0;

@@ -57,7 +57,15 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
     int64_t i = base + j;
     v[j] = i < a.n_cells ? a.counts[i] : 0;
     sum += v[j];
-    if (v[j] > a.cap && v[j] > a.n_min) a.big_list[atomicAdd(a.big_count, 1)] = (int)i;
+    if (v[j] > 0) {
+      // population class of the cell
+      if (v[j] <= a.n_min || v[j] <= a.cap_w)
+        a.warp_list[atomicAdd(a.warp_count, 1)] = (int)i;
+      else if (v[j] <= a.cap)
+        a.block_list[atomicAdd(a.block_count, 1)] = (int)i;
+      else
+        a.big_list[atomicAdd(a.big_count, 1)] = (int)i;
+    }
   }
   int total;
   int ex = block_exclusive_scan(sum, s_warp, &total);

@@ -77,6 +77,14 @@ struct Problem {
   int32_t *perm_tmp;
   int32_t max_pieces;
   int32_t *unit_next;     // ticket counters of the unit kernel, one per mode
+  // population classes: cells of at most cap_w particles (and pass-through
+  // cells) go one per warp; cells up to cap one per CTA
+  int32_t cap_w;
+  int32_t *warp_list;
+  int32_t *warp_count;
+  int32_t *warp_next;
+  int32_t *block_list;
+  int32_t *block_count;
 };
 
 // ------------------------------------------------------------ accumulators

@@ -12,6 +12,8 @@ namespace pma {
 size_t unit_smem(int mixed, int D, int cap);
 cudaError_t launch_units(const Problem &P, int mixed, int mode, int grid, cudaStream_t st);
 cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st);
+size_t warp_smem(int mixed, int D, int cap_w);
+cudaError_t launch_warps(const Problem &P, int mixed, int warps_per_cta, int grid, cudaStream_t st);
 
 // bin.cu
 struct BinArgs {
@@ -27,6 +29,11 @@ struct BinArgs {
   int32_t *unsorted;    // device flag
   int32_t *big_list;
   int32_t *big_count;
+  int32_t cap_w;
+  int32_t *warp_list;
+  int32_t *warp_count;
+  int32_t *block_list;
+  int32_t *block_count;
   unsigned *err;
   unsigned long long *scan_status;  // [scan tiles]
   int32_t *scan_ticket;

@@ -21,68 +21,9 @@
 #include "pma.h"
 #include "pma_device.cuh"
 #include "pma_launch.h"
+#include "split_common.cuh"
 
 namespace pma {
-
-constexpr int kSmall = 32;
-
-struct Item {
-  uint16_t b, e;
-  uint8_t par, depth;
-  uint16_t pad;
-};
-
-template <typename T>
-struct StoreOf {
-  __device__ static __forceinline__ T load(const void *p, int64_t i) {
-    return static_cast<const T *>(p)[i];
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ bool finite_val(T x) {
-  return isfinite(x);
-}
-
-// ------------------------------------------------------------ cut helpers
-
-template <typename T, int D>
-struct Decider;
-
-template <int D>
-struct Decider<double, D> {
-  __device__ static __forceinline__ Cut run(const Problem &P, const Moments<double, D> &M,
-                                            const double *s) {
-    double m1[D], m2[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) {
-      m1[l] = M.m1[l].v;
-      m2[l] = M.m2[l].v;
-    }
-    return decide_fp64<D>(P, M.W.v, m1, m2, s);
-  }
-  __device__ static __forceinline__ bool left(double q, const Cut &c) { return q <= c.Q; }
-};
-
-template <int D>
-struct Decider<float, D> {
-  __device__ static __forceinline__ Cut run(const Problem &P, const Moments<float, D> &M,
-                                            const float *s) {
-    return decide_mixed<D>(P, M, s);
-  }
-  __device__ static __forceinline__ bool left(float q, const Cut &c) { return q <= c.Qt; }
-};
-
-// centroid record of a merged set, from its moments (FP64 storage)
-template <int D>
-__device__ __forceinline__ void record_from_moments(const Problem &P, int64_t pos,
-                                                    const Moments<double, D> &M,
-                                                    const double *s) {
-  double W = M.W.v;
-  P.rec_w[pos] = W;
-#pragma unroll
-  for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + pos] = s[l] + M.m1[l].v / W;
-}
 
 // ---------------------------------------------------------- shared layout
 
@@ -102,10 +43,6 @@ __host__ __device__ inline size_t unit_smem_bytes(int cap) {
   size_t ids = (size_t)2 * cap * sizeof(uint16_t);
   size_t lists = (size_t)(2 * (cap / kSmall + 2) + (cap / 2 + 2)) * sizeof(Item);
   return v + ids + lists;
-}
-
-__device__ __forceinline__ int orig_index(const int32_t *perm, int64_t gb, int j) {
-  return perm ? perm[gb + j] : (int)(gb + j);
 }
 
 // ------------------------------------------------------- leaf emission
@@ -177,12 +114,6 @@ __device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const in
 #pragma unroll
     for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
   }
-}
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
 }
 
 // --------------------------------------------------------------- phase A
@@ -354,7 +285,7 @@ __global__ void __launch_bounds__(256) unit_kernel(Problem P, int mode) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (tid < kStCount) s_st[tid] = 0ull;
-  const int n_units = mode == 0 ? P.n_cells : *P.piece_count;
+  const int n_units = mode == 0 ? *P.block_count : *P.piece_count;
   const int32_t *perm = (mode == 0 && *P.unsorted == 0) ? nullptr : P.perm;
   unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};  // leaves, depth, splits, degenerate
 
@@ -367,8 +298,9 @@ __global__ void __launch_bounds__(256) unit_kernel(Problem P, int mode) {
     int64_t gb;
     int n, depth0 = 0;
     if (mode == 0) {
-      gb = P.cell_begin[u];
-      n = P.cell_begin[u + 1] - (int)gb;
+      const int c = P.block_list[u];
+      gb = P.cell_begin[c];
+      n = P.cell_begin[c + 1] - (int)gb;
       if (n == 0) continue;
       if (n <= P.n_min || n == 1) {
         for (int i = tid; i < n; i += blockDim.x) {
