@@ -295,7 +295,7 @@ def main():
     ap.add_argument("--workload", default="two_stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--fp64-only", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -346,7 +346,7 @@ def main():
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    precs = [False] if args.fp64_only else [True, False]
+    precs = {"both": [True, False], "mixed": [True], "fp64": [False]}[args.precision]
     for mixed in precs:
         q = p.astype(np.float32) if mixed else p
         results[mixed] = time_device(q, mixed, args.steps, args.warmup, dev, flush)
