@@ -98,13 +98,16 @@ struct Acc<double> {
   double v;
   __device__ __forceinline__ void zero() { v = 0.0; }
   __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
   __device__ __forceinline__ void merge(const Acc &o) { v += o.v; }
   __device__ __forceinline__ void shfl_xor(int m) { v += __shfl_xor_sync(0xffffffffu, v, m); }
   __device__ __forceinline__ double hi() const { return v; }
   __device__ __forceinline__ double value() const { return v; }
 };
 
-// compensated (Kahan) FP32 sum: value = s - c
+// compensated FP32 sum in blocks: each lane adds its own short run of terms
+// (at most a few dozen) in plain FP32; runs are combined with an error-free
+// two-sum whose rounding errors are kept in c.  value = s - c.
 template <>
 struct Acc<float> {
   float s, c;
@@ -112,12 +115,8 @@ struct Acc<float> {
     s = 0.f;
     c = 0.f;
   }
-  __device__ __forceinline__ void add(float x) {
-    float y = __fsub_rn(x, c);
-    float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-  }
+  __device__ __forceinline__ void add(float x) { s = __fadd_rn(s, x); }
+  __device__ __forceinline__ void add_prod(float a, float b) { s = __fmaf_rn(a, b, s); }
   // exact two-sum of the leading parts, errors folded into c
   __device__ __forceinline__ void merge2(float s2, float c2) {
     float t = __fadd_rn(s, s2);
@@ -157,7 +156,7 @@ struct Moments {
       T d = q[l] - s[l];
       T t = w * d;
       m1[l].add(t);
-      m2[l].add(t * d);
+      m2[l].add_prod(t, d);
     }
   }
   __device__ __forceinline__ void merge(const Moments &o) {
@@ -166,6 +165,17 @@ struct Moments {
     for (int l = 0; l < D; ++l) {
       m1[l].merge(o.m1[l]);
       m2[l].merge(o.m2[l]);
+    }
+  }
+  // sum over aligned groups of g lanes (g a power of two, <= 32)
+  __device__ __forceinline__ void group_allreduce(int g) {
+    for (int m = g >> 1; m >= 1; m >>= 1) {
+      W.shfl_xor(m);
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        m1[l].shfl_xor(m);
+        m2[l].shfl_xor(m);
+      }
     }
   }
   __device__ __forceinline__ void warp_allreduce() {
@@ -236,7 +246,7 @@ __device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const dou
 template <int D>
 __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<float, D> &M,
                                             const float *s) {
-  const float g = 1.0f / (1 << 19);  // error budget relative to the terms
+  const float g = 1.0f / (1 << 17);  // error budget relative to the terms
   float W = M.W.hi();
   float W2 = W * W;
   Cut c;
@@ -323,7 +333,7 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   c.Qt = (Ql < 0.f) ? __int_as_float(__float_as_int(Qh) - (Qh > 0.f ? 1 : (Qh < 0.f ? -1 : 0)))
                     : Qh;
   if (Qh == 0.f && Ql < 0.f) c.Qt = -__int_as_float(1);  // largest float below zero
-  c.Q = (double)Qh + (double)Ql;
+  c.Q = 0.0;  // the float path compares against Qt only
   return c;
 }
 

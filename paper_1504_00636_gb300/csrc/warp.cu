@@ -3,15 +3,20 @@
 //
 // Each warp owns one cell at a time; the warps of a CTA never wait for each
 // other.  The cell's coordinates and weights are staged once in the warp's
-// slice of shared memory (SoA columns) and stay in place; a subset is a
-// contiguous range of a 16-bit index array, and a cut writes V1 = {q_k <= Q_k}
-// to the front and V2 to the back of the same range in the other index array
-// (double-buffered by tree depth).  Leaves therefore come out in V1-first
-// depth-first order when listed by position.
-//   subsets of more than kSmall particles: the whole warp, depth-first
-//     (moments by lane-strided sums and a butterfly, cut by ballot scan);
-//   subsets of at most kSmall particles: collected 32 at a time and finished
-//     by one lane each, depth-first.
+// slice of shared memory (SoA columns) and stay in place.  A subset is a
+// contiguous range of a 16-bit index array; a cut writes V1 = {q_k <= Q_k} to
+// the front and V2 to the back of the same range in the other index array
+// (double-buffered by tree depth), so the final sets come out in V1-first
+// depth-first order when listed by position, whatever order the subsets are
+// processed in.
+//
+// Pending subsets wait on one stack per size class.  A round takes 32/G
+// subsets of one class and gives each a group of G lanes (G = 32 for the
+// largest sets down to G = 1, chosen so that a lane reads a dozen particles or
+// so): moments by lane-strided sums and a butterfly inside the group, Steps
+// 3-5, and the cut by group-masked ballots.  Two-particle sets have their own
+// round, the same arithmetic without loops.  One-particle sets are final at
+// once.
 #include "pma_device.cuh"
 #include "pma_launch.h"
 #include "split_common.cuh"
@@ -19,13 +24,43 @@
 namespace pma {
 
 constexpr int kWarpChunk = 2;  // cells taken per work-counter increment
+constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
+constexpr int kMaxCapW = 2047;
+
+// size class of a subset of m >= 2 particles
+__device__ __forceinline__ int size_class(int m) {
+  if (m == 2) return 0;
+  if (m <= 12) return 1;
+  if (m <= 24) return 2;
+  if (m <= 48) return 3;
+  if (m <= 96) return 4;
+  if (m <= 192) return 5;
+  return 6;
+}
+
+// most subsets of a class that can be pending at once (they are disjoint)
+__host__ __device__ inline int class_capacity(int c, int cap) {
+  const int lo[kClasses] = {2, 3, 13, 25, 49, 97, 193};
+  return cap / lo[c] + 1;
+}
+
+__host__ __device__ inline int stacks_entries(int cap) {
+  int t = 0;
+  for (int c = 0; c < kClasses; ++c) t += class_capacity(c, cap);
+  return t;
+}
+
+// subset record: begin (11 bits) | length (12 bits) << 11 | parity << 23
+__device__ __forceinline__ uint32_t pack_rec(int b, int m, int par) {
+  return (uint32_t)b | ((uint32_t)m << 11) | ((uint32_t)par << 23);
+}
 
 template <typename T, int D>
 struct WarpTile {
   T *data;           // [D + 1][cap]: coordinates, then weight
   uint16_t *idx[2];  // index arrays, by depth parity
-  Item *small;       // [64] pending small subsets
-  Item *stack;       // [cap / kSmall + 2] pending large subsets
+  uint32_t *stk[kClasses];
+  int *top;          // [kClasses]
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
 };
@@ -34,219 +69,232 @@ template <typename T, int D>
 __host__ __device__ inline size_t warp_region_bytes(int cap) {
   size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
-  b += (size_t)(64 + cap / kSmall + 2) * sizeof(Item);
+  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + kClasses * sizeof(int);
   return (b + 15) & ~size_t(15);
 }
-
-// ------------------------------------------------------------ leaf output
-
-// final set [b, e) of index buffer `par`: permutation, head bytes and, for a
-// merged set, its centroid record (one warp)
-template <typename T, int D>
-__device__ void warp_emit(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                          int64_t gb, int b, int e, int par, const Moments<T, D> &M, const T *s,
-                          int lane) {
-  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
-  for (int i = b + lane; i < e; i += 32) {
-    P.perm_final[gb + i] = orig_index(perm, gb, S.idx[par][i]);
-    P.head[gb + i] = (i == b) ? h : (uint8_t)0;
-  }
-  if (e - b == 1) return;
-  const int64_t hp = gb + b;
-  if constexpr (sizeof(T) == 8) {
-    if (lane == 0) record_from_moments<D>(P, hp, M, s);
-  } else {
-    double W = 0.0, S1[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) S1[l] = 0.0;
-    for (int i = b + lane; i < e; i += 32) {
-      const int j = S.idx[par][i];
-      const double w = f2d_exact(S.col(D)[j]);
-      W += w;
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(l)[j]), S1[l]);
-    }
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      W += __shfl_xor_sync(0xffffffffu, W, m);
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] += __shfl_xor_sync(0xffffffffu, S1[l], m);
-    }
-    if (lane == 0) {
-      P.rec_w[hp] = W;
-#pragma unroll
-      for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
-    }
-  }
-}
-
-// same, by one lane
-template <typename T, int D>
-__device__ void lane_emit(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                          int64_t gb, int b, int e, int par, const Moments<T, D> &M, const T *s) {
-  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
-  for (int i = b; i < e; ++i) {
-    P.perm_final[gb + i] = orig_index(perm, gb, S.idx[par][i]);
-    P.head[gb + i] = (i == b) ? h : (uint8_t)0;
-  }
-  if (e - b == 1) return;
-  const int64_t hp = gb + b;
-  if constexpr (sizeof(T) == 8) {
-    record_from_moments<D>(P, hp, M, s);
-  } else {
-    double W = 0.0, S1[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) S1[l] = 0.0;
-    for (int i = b; i < e; ++i) {
-      const int j = S.idx[par][i];
-      const double w = f2d_exact(S.col(D)[j]);
-      W += w;
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(l)[j]), S1[l]);
-    }
-    P.rec_w[hp] = W;
-#pragma unroll
-    for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
-  }
-}
-
-// ------------------------------------------------- large subsets (warp)
 
 struct Counters {
   unsigned long long leaves, depth, splits, degenerate;
 };
 
-// Steps 2-6 on one subset by the whole warp.  Returns the number of children
-// written to ch (0 when the subset is final).
+// centroid record of the merged set [b, b + m) of index buffer `par`, summed
+// over the g lanes of a group (all lanes of the warp take part; lanes with
+// nothing to record pass m = 0)
 template <typename T, int D>
-__device__ int warp_cut(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                        int64_t gb, Item it, Item *ch, Counters &cnt, int lane) {
-  const int b = it.b, e = it.e, par = it.par;
+__device__ void group_record(const Problem &P, const WarpTile<T, D> &S, int64_t gb, int b,
+                             int m, int par, int g, int gl, const Moments<T, D> &M, const T *s) {
+  if constexpr (sizeof(T) == 8) {
+    if (m > 1 && gl == 0) record_from_moments<D>(P, gb + b, M, s);
+  } else {
+    // merged W and W X, W P in FP64: a product of two floats is exact in FP64
+    double W = 0.0, S1[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) S1[l] = 0.0;
+    for (int i = gl; i < m; i += g) {
+      const int j = S.idx[par][b + i];
+      const double w = f2d_exact(S.col(D)[j]);
+      W += w;
+#pragma unroll
+      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(l)[j]), S1[l]);
+    }
+    for (int x = g >> 1; x >= 1; x >>= 1) {
+      W += __shfl_xor_sync(0xffffffffu, W, x);
+#pragma unroll
+      for (int l = 0; l < D; ++l) S1[l] += __shfl_xor_sync(0xffffffffu, S1[l], x);
+    }
+    if (m > 1 && gl == 0) {
+      P.rec_w[gb + b] = W;
+#pragma unroll
+      for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + gb + b] = S1[l] / W;
+    }
+  }
+}
+
+__device__ __forceinline__ void emit_single(const Problem &P, const int32_t *perm, int64_t gb,
+                                            int pos, int j) {
+  P.perm_final[gb + pos] = orig_index(perm, gb, j);
+  P.head[gb + pos] = kHeadSingle;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D> &S,
+                                           const int32_t *perm, int64_t gb, int b, int m,
+                                           int par, Counters &cnt) {
+  if (m == 1) {
+    emit_single(P, perm, gb, b, S.idx[par][b]);
+    cnt.leaves += 1;
+    return;
+  }
+  const int c = size_class(m);
+  const int slot = atomicAdd(&S.top[c], 1);
+  if (slot < class_capacity(c, S.cap))
+    S.stk[c][slot] = pack_rec(b, m, par);
+  else
+    set_error(P.err, kErrInternal);
+}
+
+// one round of class c >= 1: 32/G subsets, G lanes each
+template <typename T, int D>
+__device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                            int64_t gb, int c, int lane, Counters &cnt) {
+  const int lg = c - 1, G = 1 << lg, per = 32 >> lg;
+  const int avail = S.top[c];
+  const int k = min(avail, per);
+  const int gid = lane >> lg, gl = lane & (G - 1);
+  const bool act = gid < k;
+  uint32_t rec = act ? S.stk[c][avail - 1 - gid] : 0u;
+  __syncwarp();
+  if (lane == 0) S.top[c] = avail - k;
+  __syncwarp();
+  const int b = rec & 2047, m = act ? (int)((rec >> 11) & 4095) : 0, par = (rec >> 23) & 1;
+
+  // Steps 1-2: moments about the set's first particle
   T s[D];
   {
-    const int j0 = S.idx[par][b];
+    const int j0 = act ? S.idx[par][b] : 0;
 #pragma unroll
     for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
   }
   Moments<T, D> M;
   M.zero();
-  for (int i = b + lane; i < e; i += 32) {
-    const int j = S.idx[par][i];
+  for (int i = gl; i < m; i += G) {
+    const int j = S.idx[par][b + i];
     T q[D];
 #pragma unroll
     for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
     M.add(S.col(D)[j], q, s);
   }
-  M.warp_allreduce();
-  const Cut c = Decider<T, D>::run(P, M, s);
-  if (c.leaf) {
-    warp_emit<T, D>(P, S, perm, gb, b, e, par, M, s, lane);
-    if (lane == 0) {
-      cnt.leaves += 1;
-      cnt.depth += (unsigned long long)it.depth * (e - b);
-    }
-    return 0;
-  }
+  __syncwarp();
+  M.group_allreduce(G);
+  // Steps 3-5
+  Cut cut;
+  cut.leaf = 1;
+  cut.k = 0;
+  cut.Q = 0.0;
+  cut.Qt = 0.f;
+  if (act) cut = Decider<T, D>::run(P, M, s);
+  const bool split = act && !cut.leaf;
+  // Step 6: cut by group-masked ballot scan into the other index buffer
   const int np = par ^ 1;
-  const T *qk = S.col(c.k);
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
   const unsigned lt = lanemask_lt();
+  const int mmax = __reduce_max_sync(0xffffffffu, split ? (unsigned)m : 0u);
+  const T *qk = S.col(cut.k);
   int cntL = 0, cntR = 0;
-  for (int base = b; base < e; base += 32) {
-    const int i = base + lane;
-    const bool valid = i < e;
-    const int j = valid ? S.idx[par][i] : 0;
-    const bool lft = valid && Decider<T, D>::left(qk[j], c);
-    const unsigned bl = __ballot_sync(0xffffffffu, lft);
-    const unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+  for (int base = 0; base < mmax; base += G) {
+    const int i = base + gl;
+    const bool valid = split && i < m;
+    const int j = valid ? S.idx[par][b + i] : 0;
+    const bool lft = valid && Decider<T, D>::left(qk[j], cut);
+    const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
+    const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
     if (valid) {
-      const int dst = lft ? (b + cntL + __popc(bl & lt)) : (e - 1 - cntR - __popc(br & lt));
+      const int dst = lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
       S.idx[np][dst] = (uint16_t)j;
     }
     cntL += __popc(bl);
     cntR += __popc(br);
   }
   __syncwarp();
-  if (cntL == 0 || cntR == 0) {
-    // the rounded centroid lies beyond an extreme value: the set stays whole
-    warp_emit<T, D>(P, S, perm, gb, b, e, np, M, s, lane);
-    if (lane == 0) {
-      cnt.leaves += 1;
-      cnt.degenerate += 1;
-      cnt.depth += (unsigned long long)it.depth * (e - b);
+  const bool degenerate = split && (cntL == 0 || cntR == 0);
+  const bool final_set = act && (cut.leaf || degenerate);
+  const int epar = cut.leaf ? par : np;
+  // Step 7 for final sets: permutation, heads, centroid record
+  if (final_set) {
+    const uint8_t h = (m == 1) ? kHeadSingle : kHeadMerged;
+    for (int i = gl; i < m; i += G) {
+      P.perm_final[gb + b + i] = orig_index(perm, gb, S.idx[epar][b + i]);
+      P.head[gb + b + i] = (i == 0) ? h : (uint8_t)0;
     }
-    return 0;
   }
-  if (lane == 0) cnt.splits += 1;
-  const uint8_t d1 = (uint8_t)(it.depth + 1);
-  ch[0] = Item{(uint16_t)b, (uint16_t)(b + cntL), (uint8_t)np, d1, 0};
-  ch[1] = Item{(uint16_t)(b + cntL), (uint16_t)e, (uint8_t)np, d1, 0};
-  return 2;
+  if (__any_sync(0xffffffffu, final_set && m > 1))
+    group_record<T, D>(P, S, gb, b, final_set ? m : 0, epar, G, gl, M, s);
+  if (gl == 0 && act) {
+    if (final_set) {
+      cnt.leaves += 1;
+      if (degenerate) cnt.degenerate += 1;
+    } else {
+      cnt.splits += 1;
+      cnt.depth += (unsigned long long)m;
+      push_child<T, D>(P, S, perm, gb, b, cntL, np, cnt);
+      push_child<T, D>(P, S, perm, gb, b + cntL, m - cntL, np, cnt);
+    }
+  }
+  __syncwarp();
 }
 
-// ------------------------------------------------ small subsets (lane)
-
+// one round of two-particle sets, one per lane
 template <typename T, int D>
-__device__ void lane_finish(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                            int64_t gb, Item root, Counters &cnt) {
-  Item stk[kSmall + 2];
-  int sp = 0;
-  stk[sp++] = root;
-  while (sp > 0) {
-    const Item it = stk[--sp];
-    const int b = it.b, e = it.e, par = it.par;
-    if (e - b == 1) {
-      P.perm_final[gb + b] = orig_index(perm, gb, S.idx[par][b]);
-      P.head[gb + b] = kHeadSingle;
-      cnt.leaves += 1;
-      cnt.depth += it.depth;
-      continue;
-    }
-    T s[D];
-    {
-      const int j0 = S.idx[par][b];
+__device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                           int64_t gb, int lane, Counters &cnt) {
+  const int avail = S.top[0];
+  const int k = min(avail, 32);
+  const bool act = lane < k;
+  const uint32_t rec = act ? S.stk[0][avail - 1 - lane] : 0u;
+  __syncwarp();
+  if (lane == 0) S.top[0] = avail - k;
+  __syncwarp();
+  if (!act) return;
+  const int b = rec & 2047, par = (rec >> 23) & 1;
+  const int ja = S.idx[par][b], jb = S.idx[par][b + 1];
+  T qa[D], qb[D];
 #pragma unroll
-      for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
-    }
-    Moments<T, D> M;
-    M.zero();
-    for (int i = b; i < e; ++i) {
-      const int j = S.idx[par][i];
-      T q[D];
+  for (int l = 0; l < D; ++l) {
+    qa[l] = S.col(l)[ja];
+    qb[l] = S.col(l)[jb];
+  }
+  const T wa = S.col(D)[ja], wb = S.col(D)[jb];
+  // the same sums as the general path takes for two particles
+  Moments<T, D> M;
+  M.zero();
+  M.add(wa, qa, qa);
+  M.add(wb, qb, qa);
+  const Cut cut = Decider<T, D>::run(P, M, qa);
+  bool merged = cut.leaf != 0;
+  int first = ja, second = jb;
+  if (!merged) {
+    T ka = qa[0], kb = qb[0];
 #pragma unroll
-      for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
-      M.add(S.col(D)[j], q, s);
-    }
-    const Cut c = Decider<T, D>::run(P, M, s);
-    if (c.leaf) {
-      lane_emit<T, D>(P, S, perm, gb, b, e, par, M, s);
-      cnt.leaves += 1;
-      cnt.depth += (unsigned long long)it.depth * (e - b);
-      continue;
-    }
-    const int np = par ^ 1;
-    const T *qk = S.col(c.k);
-    int cntL = 0, cntR = 0;
-    for (int i = b; i < e; ++i) {
-      const int j = S.idx[par][i];
-      const bool lft = Decider<T, D>::left(qk[j], c);
-      const int dst = lft ? (b + cntL++) : (e - 1 - cntR++);
-      S.idx[np][dst] = (uint16_t)j;
-    }
-    if (cntL == 0 || cntR == 0) {
-      lane_emit<T, D>(P, S, perm, gb, b, e, np, M, s);
-      cnt.leaves += 1;
+    for (int l = 0; l < D; ++l)
+      if (l == cut.k) {
+        ka = qa[l];
+        kb = qb[l];
+      }
+    const bool la = Decider<T, D>::left(ka, cut), lb = Decider<T, D>::left(kb, cut);
+    if (la == lb) {
+      merged = true;  // degenerate cut: the set stays whole
       cnt.degenerate += 1;
-      cnt.depth += (unsigned long long)it.depth * (e - b);
-      continue;
+    } else if (!la) {
+      first = jb;
+      second = ja;
     }
+  }
+  P.perm_final[gb + b] = orig_index(perm, gb, first);
+  P.perm_final[gb + b + 1] = orig_index(perm, gb, second);
+  if (merged) {
+    P.head[gb + b] = kHeadMerged;
+    P.head[gb + b + 1] = 0;
+    cnt.leaves += 1;
+    double W, C[D];
+    if constexpr (sizeof(T) == 8) {
+      W = (double)wa + (double)wb;
+#pragma unroll
+      for (int l = 0; l < D; ++l) C[l] = qa[l] + M.m1[l].v / W;
+    } else {
+      const double da = f2d_exact(wa), db = f2d_exact(wb);
+      W = da + db;
+#pragma unroll
+      for (int l = 0; l < D; ++l) C[l] = fma(da, f2d_exact(qa[l]), db * f2d_exact(qb[l])) / W;
+    }
+    P.rec_w[gb + b] = W;
+#pragma unroll
+    for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + gb + b] = C[l];
+  } else {
+    P.head[gb + b] = kHeadSingle;
+    P.head[gb + b + 1] = kHeadSingle;
+    cnt.leaves += 2;
     cnt.splits += 1;
-    if (sp + 2 > kSmall + 2) {
-      set_error(P.err, kErrInternal);
-      return;
-    }
-    const uint8_t d1 = (uint8_t)(it.depth + 1);
-    stk[sp++] = Item{(uint16_t)(b + cntL), (uint16_t)e, (uint8_t)np, d1, 0};
-    stk[sp++] = Item{(uint16_t)b, (uint16_t)(b + cntL), (uint8_t)np, d1, 0};
+    cnt.depth += 2;
   }
 }
 
@@ -263,13 +311,17 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
     S.data = reinterpret_cast<T *>(base);
     S.idx[0] = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
     S.idx[1] = S.idx[0] + cap;
-    size_t off = ((size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t) + 15) &
-                 ~size_t(15);
-    S.small = reinterpret_cast<Item *>(base + off);
-    S.stack = S.small + 64;
+    const size_t off =
+        ((size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t) + 15) &
+        ~size_t(15);
+    uint32_t *st = reinterpret_cast<uint32_t *>(base + off);
+    for (int c = 0; c < kClasses; ++c) {
+      S.stk[c] = st;
+      st += class_capacity(c, cap);
+    }
+    S.top = reinterpret_cast<int *>(st);
     S.cap = cap;
   }
-  const int max_stack = cap / kSmall + 2;
   const int32_t *perm = (*P.unsorted == 0) ? nullptr : P.perm;
   const int count = *P.warp_count;
   Counters cnt{0ull, 0ull, 0ull, 0ull};
@@ -287,10 +339,7 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
       const int n = P.cell_begin[cell + 1] - (int)gb;
       if (n <= P.n_min || n == 1) {
         // Sec. 3 "Input": cells with at most N_min particles are not merged
-        for (int i = lane; i < n; i += 32) {
-          P.perm_final[gb + i] = orig_index(perm, gb, i);
-          P.head[gb + i] = kHeadSingle;
-        }
+        for (int i = lane; i < n; i += 32) emit_single(P, perm, gb, i, i);
         passed += 1;
         continue;
       }
@@ -310,58 +359,28 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
         S.idx[0][i] = (uint16_t)i;
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
+      if (lane < kClasses) S.top[lane] = 0;
       __syncwarp();
-      const Item root{0, (uint16_t)n, 0, 0, 0};
-      int sp = 0, ns = 0;
-      if (n <= kSmall) {
-        if (lane == 0) S.small[0] = root;
-        ns = 1;
-      } else {
-        if (lane == 0) S.stack[0] = root;
-        sp = 1;
+      if (lane == 0) {
+        const int c = size_class(n);
+        S.stk[c][0] = pack_rec(0, n, 0);
+        S.top[c] = 1;
       }
       __syncwarp();
       for (;;) {
-        if (ns >= 32 || (sp == 0 && ns > 0)) {
-          // one round of small subsets, one per lane
-          const int take = min(ns, 32);
-          if (lane < take) lane_finish<T, D>(P, S, perm, gb, S.small[lane], cnt);
-          __syncwarp();
-          if (lane == 0)
-            for (int k = take; k < ns; ++k) S.small[k - take] = S.small[k];
-          ns -= take;
-          __syncwarp();
-          continue;
-        }
-        if (sp == 0) break;
-        const Item it = S.stack[--sp];
-        Item ch[2];
-        const int nch = warp_cut<T, D>(P, S, perm, gb, it, ch, cnt, lane);
-        for (int h = 0; h < nch; ++h) {
-          const int m = ch[h].e - ch[h].b;
-          if (m == 1) {
-            if (lane == 0) {
-              P.perm_final[gb + ch[h].b] = orig_index(perm, gb, S.idx[ch[h].par][ch[h].b]);
-              P.head[gb + ch[h].b] = kHeadSingle;
-              cnt.leaves += 1;
-              cnt.depth += ch[h].depth;
-            }
-          } else if (m <= kSmall) {
-            if (lane == 0) S.small[ns] = ch[h];
-            ++ns;
-          } else if (sp < max_stack) {
-            if (lane == 0) S.stack[sp] = ch[h];
-            ++sp;
-          } else {
-            if (lane == 0) set_error(P.err, kErrInternal);
-          }
-        }
+        int c = -1;
+#pragma unroll
+        for (int k = kClasses - 1; k >= 0; --k)
+          if (c < 0 && S.top[k] > 0) c = k;
+        if (c < 0) break;
+        if (c == 0)
+          pair_round<T, D>(P, S, perm, gb, lane, cnt);
+        else
+          group_round<T, D>(P, S, perm, gb, c, lane, cnt);
         __syncwarp();
       }
     }
   }
-  // counters: lane-level work is spread over the lanes, warp-level work
-  // was counted by lane 0 only
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) {
     cnt.leaves += __shfl_xor_sync(0xffffffffu, cnt.leaves, m);
@@ -398,6 +417,7 @@ size_t warp_smem(int mixed, int D, int cap_w) {
 
 template <typename T, int D>
 static cudaError_t launch_warps_t(const Problem &P, int wpc, int grid, cudaStream_t st) {
+  if (P.cap_w > kMaxCapW) return cudaErrorInvalidValue;
   const size_t smem = (size_t)wpc * warp_region_bytes<T, D>(P.cap_w);
   cudaError_t e = cudaFuncSetAttribute(warp_kernel<T, D>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
