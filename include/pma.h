@@ -165,9 +165,9 @@ int pma_get_timing(const pma_handle *h, float *ms, int n);
  * PIC code whose device memory is owned by its own pool allocator, or a
  * host thread that must not trigger the implicit device synchronisation
  * that cudaMalloc/cudaFree can cause in the middle of a time step.  It
- * needs no handle: its scratch is a fixed array inside the library (about
- * 4.5 MB, held by every GPU that loads the library until the process
- * exits), and the caller passes only inputs and outputs.
+ * needs no handle: its scratch is a fixed array inside the library (under
+ * 1 MB, held by every GPU that loads the library until the process exits),
+ * and the caller passes only inputs and outputs.
  *   cfg          dx, dp, cell_size, n_cells, n_min and precision as for
  *                pma_create (capacity and flags are ignored)
  *   n, cells, pos, mom, weights, tol_x, tol_p   as for pma_merge; the cell

@@ -77,7 +77,6 @@ struct pma_handle {
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
   int32_t *warp_list = nullptr, *block_list = nullptr;
   uint8_t *head = nullptr;
-  double *rec_w = nullptr, *rec_c = nullptr;
   unsigned long long *bin_status = nullptr, *emit_status = nullptr;
   int4 *pieces = nullptr;
   Ctl *ctl = nullptr;
@@ -118,7 +117,7 @@ cudaError_t dalloc(T **p, size_t count) {
 
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
-                  h->big_list, h->head, h->rec_w, h->rec_c, h->bin_status, h->emit_status,
+                  h->big_list, h->head, h->bin_status, h->emit_status,
                   h->pieces, h->ctl, h->warp_list, h->block_list, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
@@ -234,8 +233,6 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
-            dalloc(&h->rec_w, N) == cudaSuccess &&
-            dalloc(&h->rec_c, (size_t)N * h->D) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->emit_status, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
@@ -346,9 +343,6 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.perm = h->perm;
   P.head = h->head;
   P.perm_final = h->perm_final;
-  P.rec_w = h->rec_w;
-  P.rec_c = h->rec_c;
-  P.stride = h->capacity;
   P.err = &h->ctl->err;
   P.stats = h->ctl->stats;
   P.big_list = h->big_list;
@@ -386,9 +380,6 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.mixed = h->mixed;
   m.head = h->head;
   m.perm_final = h->perm_final;
-  m.rec_w = h->rec_w;
-  m.rec_c = h->rec_c;
-  m.stride = h->capacity;
   m.cells = cells;
   for (int l = 0; l < h->D; ++l) m.q[l] = P.q[l];
   m.w = weights;

@@ -1,5 +1,6 @@
 // Step 7: replace every final set by its centroid, compacted in canonical
-// order.  The final sets of all cells are contiguous position ranges marked by
+// order; the centroid (W, X, P) of a merged set is summed here from its
+// members, in FP64.  The final sets of all cells are contiguous position ranges marked by
 // a head byte at their first position; cells are laid out in ascending order
 // and the sets of a cell in V1-first depth-first order, so the output slot of
 // a set is the number of heads before it.  One pass: each tile counts its
@@ -101,10 +102,28 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       bad |= !(w > T(0)) || !isfinite(w);
       a.out_w[slot] = to_f64<T>(w);
     } else {
-      a.out_w[slot] = a.rec_w[p];
-      for (int l = 0; l < a.dx; ++l)
-        static_cast<T *>(a.out_pos[l])[slot] = (T)a.rec_c[l * a.stride + p];
-      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot] = a.rec_c[(a.dx + l) * a.stride + p];
+      // merged set: its members are the positions up to the next head.
+      // W, W X and W P are FP64 sums; a product of two floats is exact in FP64.
+      double W = 0.0, S1[kMaxD];
+#pragma unroll
+      for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
+      const int D = a.dx + a.dp;
+      for (int64_t r = p; r < a.n; ++r) {
+        if (r > p && a.head[r]) break;
+        const int o = a.perm_final[r];
+        if ((unsigned)o >= (unsigned)a.n) {
+          internal = true;
+          break;
+        }
+        const double w = to_f64<T>(static_cast<const T *>(a.w)[o]);
+        W += w;
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.q[l])[o]), S1[l]);
+      }
+      a.out_w[slot] = W;
+      for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot] = (T)(S1[l] / W);
+      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot] = S1[a.dx + l] / W;
     }
   }
   if (bad) atomicOr(a.err, kErrInput);

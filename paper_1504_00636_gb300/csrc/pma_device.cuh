@@ -40,8 +40,7 @@ enum Stat {
 };
 
 // head byte of a final position: 0 inside a final set, 1 first (only)
-// particle of a one-particle set, 2 first particle of a merged set whose
-// centroid record sits at that position
+// particle of a one-particle set, 2 first particle of a merged set
 constexpr uint8_t kHeadSingle = 1;
 constexpr uint8_t kHeadMerged = 2;
 
@@ -63,9 +62,6 @@ struct Problem {
   int32_t *perm;          // sorted position -> input index (workspace)
   uint8_t *head;          // [N] head byte per final position
   int32_t *perm_final;    // [N] input index at each final position
-  double *rec_w;          // [N] centroid weight at merged-set heads
-  double *rec_c;          // [D][stride] centroid coordinates
-  int64_t stride;
   unsigned *err;          // device status word
   unsigned long long *stats;
   // big cells: cells above `cap` are cut in global memory first
@@ -253,7 +249,9 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   c.leaf = 1;
   c.k = 0;
   bool sure = true;
-  float r[D];
+  // first and second largest Delta^2 (position: V / (L W)^2, momentum:
+  // V / (W P)^2; den = 0 is +infinity unless V = 0)
+  float r1 = -1.f, r2 = -1.f;
 #pragma unroll
   for (int l = 0; l < D; ++l) {
     float m1 = M.m1[l].hi(), m2 = M.m2[l].hi();
@@ -275,25 +273,24 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
     float f = V - tol2 * den;
     if (fabsf(f) <= eV + tol2 * eD) sure = false;
     if (f > 0.f) c.leaf = 0;
-    // Delta^2 with relative uncertainty; den = 0 means infinity unless V = 0
+    float r;
     if (V == 0.f)
-      r[l] = 0.f;
+      r = 0.f;
     else if (den <= eD)
-      r[l] = __int_as_float(0x7f800000);
+      r = __int_as_float(0x7f800000);
     else
-      r[l] = V / den;
+      r = __fdividef(V, den);
     if (V != 0.f && (V <= eV || den <= eD)) sure = false;
+    if (r > r1) {
+      r2 = r1;
+      r1 = r;
+      c.k = l;
+    } else if (r > r2) {
+      r2 = r;
+    }
   }
-  if (!c.leaf) {
-    int k = 0;
-#pragma unroll
-    for (int l = 1; l < D; ++l)
-      if (r[l] > r[k]) k = l;
-    c.k = k;
-#pragma unroll
-    for (int l = 0; l < D; ++l)
-      if (l != k && r[l] >= r[k] * (1.f - 64.f * g)) sure = false;
-  }
+  // the runner-up axis within the error budget: FP64 decides
+  if (!c.leaf && r2 >= r1 * (1.f - 16.f * g)) sure = false;
   if (!sure) {
     double W64 = M.W.value(), m1d[D], m2d[D], sd[D];
 #pragma unroll

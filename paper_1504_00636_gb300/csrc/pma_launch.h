@@ -48,9 +48,6 @@ struct EmitArgs {
   int32_t dx, dp, mixed;
   const uint8_t *head;
   const int32_t *perm_final;
-  const double *rec_w;
-  const double *rec_c;
-  int64_t stride;
   const int32_t *cells;
   const void *q[kMaxD];
   const void *w;

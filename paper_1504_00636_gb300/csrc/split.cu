@@ -47,7 +47,8 @@ __host__ __device__ inline size_t unit_smem_bytes(int cap) {
 
 // ------------------------------------------------------- leaf emission
 
-// merged set [b, e) of buffer `par`, by one warp
+// final set [b, e) of buffer `par`, by one warp: permutation and head
+// bytes (the emit kernel sums merged sets up)
 template <typename T, int D>
 __device__ void emit_leaf_warp(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
                                int64_t gb, int b, int e, int par, const Moments<T, D> &M,
@@ -57,36 +58,9 @@ __device__ void emit_leaf_warp(const Problem &P, const Tile<T, D> &S, const int3
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
   }
-  int64_t hp = gb + b;
-  if (e - b == 1) return;
-  if constexpr (sizeof(T) == 8) {
-    if (lane == 0) record_from_moments<D>(P, hp, M, s);
-  } else {
-    // merged W and P in FP64: products of two floats are exact in FP64
-    double W = 0.0, S1[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) S1[l] = 0.0;
-    for (int j = b + lane; j < e; j += 32) {
-      double w = f2d_exact(S.col(par, D)[j]);
-      W += w;
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(par, l)[j]), S1[l]);
-    }
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-      W += __shfl_xor_sync(0xffffffffu, W, m);
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] += __shfl_xor_sync(0xffffffffu, S1[l], m);
-    }
-    if (lane == 0) {
-      P.rec_w[hp] = W;
-#pragma unroll
-      for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
-    }
-  }
 }
 
-// merged set [b, e) of buffer `par`, by one thread
+// same, by one thread
 template <typename T, int D>
 __device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
                                  int64_t gb, int b, int e, int par, const Moments<T, D> &M,
@@ -95,24 +69,6 @@ __device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const in
   for (int j = b; j < e; ++j) {
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
-  }
-  int64_t hp = gb + b;
-  if (e - b == 1) return;
-  if constexpr (sizeof(T) == 8) {
-    record_from_moments<D>(P, hp, M, s);
-  } else {
-    double W = 0.0, S1[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) S1[l] = 0.0;
-    for (int j = b; j < e; ++j) {
-      double w = f2d_exact(S.col(par, D)[j]);
-      W += w;
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(par, l)[j]), S1[l]);
-    }
-    P.rec_w[hp] = W;
-#pragma unroll
-    for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + hp] = S1[l] / W;
   }
 }
 
@@ -426,7 +382,6 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
   __shared__ int s_sp, s_ticket;
   __shared__ BlockMoments<T, D> sh;
   __shared__ int s_wcnt[2][16];
-  __shared__ double s_red[16][D + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
   for (;;) {
@@ -508,48 +463,7 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
           P.perm_final[i] = P.perm[i];
           P.head[i] = (i == b) ? ((e - b == 1) ? kHeadSingle : kHeadMerged) : (uint8_t)0;
         }
-        // merged W, X, P in FP64
-        double acc[D + 1];
-        if constexpr (sizeof(T) == 8) {
-          acc[0] = M.W.value();
-#pragma unroll
-          for (int l = 0; l < D; ++l) acc[l + 1] = s[l] * acc[0] + M.m1[l].value();
-        } else {
-#pragma unroll
-          for (int l = 0; l <= D; ++l) acc[l] = 0.0;
-          for (int64_t i = b + tid; i < e; i += blockDim.x) {
-            int src = P.perm[i];
-            double w = f2d_exact(StoreOf<T>::load(P.w, src));
-            acc[0] += w;
-#pragma unroll
-            for (int l = 0; l < D; ++l)
-              acc[l + 1] = fma(w, f2d_exact(StoreOf<T>::load(P.q[l], src)), acc[l + 1]);
-          }
-#pragma unroll
-          for (int m = 16; m >= 1; m >>= 1)
-#pragma unroll
-            for (int l = 0; l <= D; ++l) acc[l] += __shfl_xor_sync(0xffffffffu, acc[l], m);
-          __syncthreads();
-          if (lane == 0)
-#pragma unroll
-            for (int l = 0; l <= D; ++l) s_red[warp][l] = acc[l];
-          __syncthreads();
-          if (tid == 0)
-            for (int k = 1; k < nw; ++k)
-#pragma unroll
-              for (int l = 0; l <= D; ++l) acc[l] += s_red[k][l];
-        }
         if (tid == 0) {
-          if (sizeof(T) == 8) {
-            P.rec_w[b] = M.W.value();
-#pragma unroll
-            for (int l = 0; l < D; ++l)
-              P.rec_c[l * P.stride + b] = (double)s[l] + M.m1[l].value() / M.W.value();
-          } else {
-            P.rec_w[b] = acc[0];
-#pragma unroll
-            for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + b] = acc[l + 1] / acc[0];
-          }
           atomicAdd(&P.stats[kStLeaves], 1ull);
           atomicAdd(&P.stats[kStDepth], (unsigned long long)it.z * (e - b));
         }
@@ -667,8 +581,6 @@ struct NoAllocScratch {
   unsigned long long stats[kStCount];
   // written before being read within a call
   int32_t perm_final[PMA_NOALLOC_MAX_N];
-  double rec_w[PMA_NOALLOC_MAX_N];
-  double rec_c[kMaxD * PMA_NOALLOC_MAX_N];
   uint8_t head[PMA_NOALLOC_MAX_N];
 };
 constexpr size_t kNoAllocZeroBytes = offsetof(NoAllocScratch, perm_final);
@@ -843,10 +755,27 @@ __global__ void __launch_bounds__(256) noalloc_kernel(Problem P, NoAllocScratch 
         if (!(w > T(0)) || !finite_val(w)) atomicOr(&Sc->err, kErrInput);
         o.w[slot] = sizeof(T) == 4 ? f2d_exact((float)w) : (double)w;
       } else {
-        o.w[slot] = P.rec_w[gp];
-        for (int l = 0; l < P.dx; ++l)
-          static_cast<T *>(o.pos[l])[slot] = (T)P.rec_c[l * P.stride + gp];
-        for (int l = 0; l < P.D - P.dx; ++l) o.mom[l][slot] = P.rec_c[(P.dx + l) * P.stride + gp];
+        // merged set: FP64 sums over its members (positions up to the next
+        // head of the cell)
+        double W = 0.0, S1[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) S1[l] = 0.0;
+        for (int r = p; r < m; ++r) {
+          if (r > p && P.head[gb + r]) break;
+          const int om = P.perm_final[gb + r];
+          if ((unsigned)om >= (unsigned)n) break;
+          const T wm = StoreOf<T>::load(P.w, om);
+          const double wd = sizeof(T) == 4 ? f2d_exact((float)wm) : (double)wm;
+          W += wd;
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const T x = StoreOf<T>::load(P.q[l], om);
+            S1[l] = fma(wd, sizeof(T) == 4 ? f2d_exact((float)x) : (double)x, S1[l]);
+          }
+        }
+        o.w[slot] = W;
+        for (int l = 0; l < P.dx; ++l) static_cast<T *>(o.pos[l])[slot] = (T)(S1[l] / W);
+        for (int l = 0; l < P.D - P.dx; ++l) o.mom[l][slot] = S1[P.dx + l] / W;
       }
     }
   }
@@ -959,9 +888,6 @@ extern "C" int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t
   P.cells = cells;
   P.head = Sc->head;
   P.perm_final = Sc->perm_final;
-  P.rec_w = Sc->rec_w;
-  P.rec_c = Sc->rec_c;
-  P.stride = PMA_NOALLOC_MAX_N;
   P.err = &Sc->err;
   P.stats = Sc->stats;
   NoAllocOut o{};

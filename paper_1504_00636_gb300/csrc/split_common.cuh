@@ -57,17 +57,6 @@ struct Decider<float, D> {
   __device__ static __forceinline__ bool left(float q, const Cut &c) { return q <= c.Qt; }
 };
 
-// centroid record of a merged set, from its moments (FP64 storage)
-template <int D>
-__device__ __forceinline__ void record_from_moments(const Problem &P, int64_t pos,
-                                                    const Moments<double, D> &M,
-                                                    const double *s) {
-  double W = M.W.v;
-  P.rec_w[pos] = W;
-#pragma unroll
-  for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + pos] = s[l] + M.m1[l].v / W;
-}
-
 __device__ __forceinline__ int orig_index(const int32_t *perm, int64_t gb, int j) {
   return perm ? perm[gb + j] : (int)(gb + j);
 }

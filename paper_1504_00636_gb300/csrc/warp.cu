@@ -77,39 +77,6 @@ struct Counters {
   unsigned long long leaves, depth, splits, degenerate;
 };
 
-// centroid record of the merged set [b, b + m) of index buffer `par`, summed
-// over the g lanes of a group (all lanes of the warp take part; lanes with
-// nothing to record pass m = 0)
-template <typename T, int D>
-__device__ void group_record(const Problem &P, const WarpTile<T, D> &S, int64_t gb, int b,
-                             int m, int par, int g, int gl, const Moments<T, D> &M, const T *s) {
-  if constexpr (sizeof(T) == 8) {
-    if (m > 1 && gl == 0) record_from_moments<D>(P, gb + b, M, s);
-  } else {
-    // merged W and W X, W P in FP64: a product of two floats is exact in FP64
-    double W = 0.0, S1[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) S1[l] = 0.0;
-    for (int i = gl; i < m; i += g) {
-      const int j = S.idx[par][b + i];
-      const double w = f2d_exact(S.col(D)[j]);
-      W += w;
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] = fma(w, f2d_exact(S.col(l)[j]), S1[l]);
-    }
-    for (int x = g >> 1; x >= 1; x >>= 1) {
-      W += __shfl_xor_sync(0xffffffffu, W, x);
-#pragma unroll
-      for (int l = 0; l < D; ++l) S1[l] += __shfl_xor_sync(0xffffffffu, S1[l], x);
-    }
-    if (m > 1 && gl == 0) {
-      P.rec_w[gb + b] = W;
-#pragma unroll
-      for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + gb + b] = S1[l] / W;
-    }
-  }
-}
-
 __device__ __forceinline__ void emit_single(const Problem &P, const int32_t *perm, int64_t gb,
                                             int pos, int j) {
   P.perm_final[gb + pos] = orig_index(perm, gb, j);
@@ -157,6 +124,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   }
   Moments<T, D> M;
   M.zero();
+#pragma unroll 2
   for (int i = gl; i < m; i += G) {
     const int j = S.idx[par][b + i];
     T q[D];
@@ -176,30 +144,41 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   const bool split = act && !cut.leaf;
   // Step 6: cut by group-masked ballot scan into the other index buffer
   const int np = par ^ 1;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
-  const unsigned lt = lanemask_lt();
-  const int mmax = __reduce_max_sync(0xffffffffu, split ? (unsigned)m : 0u);
   const T *qk = S.col(cut.k);
   int cntL = 0, cntR = 0;
-  for (int base = 0; base < mmax; base += G) {
-    const int i = base + gl;
-    const bool valid = split && i < m;
-    const int j = valid ? S.idx[par][b + i] : 0;
-    const bool lft = valid && Decider<T, D>::left(qk[j], cut);
-    const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
-    const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
-    if (valid) {
-      const int dst = lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
-      S.idx[np][dst] = (uint16_t)j;
+  if (G == 1) {
+    // one lane per set: a serial stable-front / reversed-back partition
+    if (split)
+      for (int i = 0; i < m; ++i) {
+        const int j = S.idx[par][b + i];
+        const int dst = Decider<T, D>::left(qk[j], cut) ? (b + cntL++) : (b + m - 1 - cntR++);
+        S.idx[np][dst] = (uint16_t)j;
+      }
+  } else {
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
+    const unsigned lt = lanemask_lt();
+    const int mmax = __reduce_max_sync(0xffffffffu, split ? (unsigned)m : 0u);
+    for (int base = 0; base < mmax; base += G) {
+      const int i = base + gl;
+      const bool valid = split && i < m;
+      const int j = valid ? S.idx[par][b + i] : 0;
+      const bool lft = valid && Decider<T, D>::left(qk[j], cut);
+      const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
+      const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
+      if (valid) {
+        const int dst =
+            lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
+        S.idx[np][dst] = (uint16_t)j;
+      }
+      cntL += __popc(bl);
+      cntR += __popc(br);
     }
-    cntL += __popc(bl);
-    cntR += __popc(br);
   }
   __syncwarp();
   const bool degenerate = split && (cntL == 0 || cntR == 0);
   const bool final_set = act && (cut.leaf || degenerate);
   const int epar = cut.leaf ? par : np;
-  // Step 7 for final sets: permutation, heads, centroid record
+  // final sets: permutation and head bytes (Step 7 sums them up later)
   if (final_set) {
     const uint8_t h = (m == 1) ? kHeadSingle : kHeadMerged;
     for (int i = gl; i < m; i += G) {
@@ -207,8 +186,6 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
       P.head[gb + b + i] = (i == 0) ? h : (uint8_t)0;
     }
   }
-  if (__any_sync(0xffffffffu, final_set && m > 1))
-    group_record<T, D>(P, S, gb, b, final_set ? m : 0, epar, G, gl, M, s);
   if (gl == 0 && act) {
     if (final_set) {
       cnt.leaves += 1;
@@ -275,20 +252,6 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
     P.head[gb + b] = kHeadMerged;
     P.head[gb + b + 1] = 0;
     cnt.leaves += 1;
-    double W, C[D];
-    if constexpr (sizeof(T) == 8) {
-      W = (double)wa + (double)wb;
-#pragma unroll
-      for (int l = 0; l < D; ++l) C[l] = qa[l] + M.m1[l].v / W;
-    } else {
-      const double da = f2d_exact(wa), db = f2d_exact(wb);
-      W = da + db;
-#pragma unroll
-      for (int l = 0; l < D; ++l) C[l] = fma(da, f2d_exact(qa[l]), db * f2d_exact(qb[l])) / W;
-    }
-    P.rec_w[gb + b] = W;
-#pragma unroll
-    for (int l = 0; l < D; ++l) P.rec_c[l * P.stride + gb + b] = C[l];
   } else {
     P.head[gb + b] = kHeadSingle;
     P.head[gb + b + 1] = kHeadSingle;
