@@ -35,8 +35,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   __shared__ long long s_prefix;
   __shared__ unsigned short s_mask[kEmitThreads];
   __shared__ int s_chunk[kEmitThreads];
+  __shared__ int s_nmerged;
+  __shared__ int2 s_merged[kEmitTile / 2 + 1];  // (offset in tile, output slot)
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(a.scan_ticket, 1);
+  if (tid == 0) {
+    s_tile = atomicAdd(a.scan_ticket, 1);
+    s_nmerged = 0;
+  }
   __syncthreads();
   const int tile = s_tile;
   const int64_t t0 = (int64_t)tile * kEmitTile;
@@ -102,29 +107,37 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       bad |= !(w > T(0)) || !isfinite(w);
       a.out_w[slot] = to_f64<T>(w);
     } else {
-      // merged set: its members are the positions up to the next head.
-      // W, W X and W P are FP64 sums; a product of two floats is exact in FP64.
-      double W = 0.0, S1[kMaxD];
-#pragma unroll
-      for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
-      const int D = a.dx + a.dp;
-      for (int64_t r = p; r < a.n; ++r) {
-        if (r > p && a.head[r]) break;
-        const int o = a.perm_final[r];
-        if ((unsigned)o >= (unsigned)a.n) {
-          internal = true;
-          break;
-        }
-        const double w = to_f64<T>(static_cast<const T *>(a.w)[o]);
-        W += w;
-#pragma unroll
-        for (int l = 0; l < kMaxD; ++l)
-          if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.q[l])[o]), S1[l]);
-      }
-      a.out_w[slot] = W;
-      for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot] = (T)(S1[l] / W);
-      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot] = S1[a.dx + l] / W;
+      // merged set: summed below, densely, by the whole CTA
+      const int k = atomicAdd(&s_nmerged, 1);
+      s_merged[k] = make_int2((int)(p - t0), (int)slot);
     }
+  }
+  __syncthreads();
+  // merged sets of this tile: members are the positions up to the next head;
+  // W, W X and W P are FP64 sums (a product of two floats is exact in FP64)
+  const int D = a.dx + a.dp;
+  for (int k = tid; k < s_nmerged; k += kEmitThreads) {
+    const int64_t p = t0 + s_merged[k].x;
+    const long long slot = s_merged[k].y;
+    double W = 0.0, S1[kMaxD];
+#pragma unroll
+    for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
+    for (int64_t r = p; r < a.n; ++r) {
+      if (r > p && a.head[r]) break;
+      const int o = a.perm_final[r];
+      if ((unsigned)o >= (unsigned)a.n) {
+        internal = true;
+        break;
+      }
+      const double w = to_f64<T>(static_cast<const T *>(a.w)[o]);
+      W += w;
+#pragma unroll
+      for (int l = 0; l < kMaxD; ++l)
+        if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.q[l])[o]), S1[l]);
+    }
+    a.out_w[slot] = W;
+    for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot] = (T)(S1[l] / W);
+    for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot] = S1[a.dx + l] / W;
   }
   if (bad) atomicOr(a.err, kErrInput);
   if (internal) atomicOr(a.err, kErrInternal);
