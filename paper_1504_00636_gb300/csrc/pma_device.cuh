@@ -334,15 +334,30 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   return c;
 }
 
-// FP32 -> FP64 without the FP64 pipe (exact for every finite float).
+// FP32 -> FP64 exactly, with integer operations only (no FP64 pipe):
+// normal numbers rebias the exponent, subnormals are normalised, zero, inf
+// and nan keep their class.
 __device__ __forceinline__ double f2d_exact(float f) {
-  unsigned u = __float_as_uint(f);
-  unsigned e = (u >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;  // zero, subnormal, inf, nan
-  unsigned long long s = (unsigned long long)(u >> 31) << 63;
-  unsigned long long ee = (unsigned long long)(e + 896u) << 52;
-  unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
-  return __longlong_as_double((long long)(s | ee | m));
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  unsigned long long ee, mm;
+  if (e != 0u && e != 0xffu) {
+    ee = (unsigned long long)(e + 896u) << 52;
+    mm = (unsigned long long)m << 29;
+  } else if (e == 0xffu) {
+    ee = 0x7ffull << 52;
+    mm = (unsigned long long)m << 29;
+  } else if (m == 0u) {
+    ee = 0ull;
+    mm = 0ull;
+  } else {
+    const int msb = 31 - __clz(m);  // value = m 2^-149 = 1.f 2^(msb - 149)
+    ee = (unsigned long long)(msb + 874) << 52;
+    mm = (unsigned long long)((m << (23 - msb)) & 0x7fffffu) << 29;
+  }
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  return __longlong_as_double((long long)(sign | ee | mm));
 }
 
 __device__ __forceinline__ void set_error(unsigned *err, unsigned bit) { atomicOr(err, bit); }

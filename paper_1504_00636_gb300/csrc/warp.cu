@@ -23,7 +23,7 @@
 
 namespace pma {
 
-constexpr int kWarpChunk = 2;  // cells taken per work-counter increment
+constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
 constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
 constexpr int kMaxCapW = 2047;
 
@@ -124,7 +124,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   }
   Moments<T, D> M;
   M.zero();
-#pragma unroll 2
+#pragma unroll 4
   for (int i = gl; i < m; i += G) {
     const int j = S.idx[par][b + i];
     T q[D];
@@ -149,6 +149,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   if (G == 1) {
     // one lane per set: a serial stable-front / reversed-back partition
     if (split)
+#pragma unroll 4
       for (int i = 0; i < m; ++i) {
         const int j = S.idx[par][b + i];
         const int dst = Decider<T, D>::left(qk[j], cut) ? (b + cntL++) : (b + m - 1 - cntR++);
@@ -307,7 +308,22 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
         continue;
       }
       merged += 1;
+      if (t + 1 < c1 && !perm && lane < D + 1) {
+        // the next cell of this chunk: pull its columns into L2 meanwhile
+        const int nc = P.warp_list[t + 1];
+        const int64_t nb = P.cell_begin[nc], ne = P.cell_begin[nc + 1];
+        const size_t es = sizeof(T);
+        const char *col = static_cast<const char *>(lane < D ? P.q[lane] : P.w);
+        // the 16-byte-aligned part of the range only: never outside the array
+        const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nb * es) + 15) & ~uintptr_t(15);
+        const uintptr_t a1 = (reinterpret_cast<uintptr_t>(col + ne * es)) & ~uintptr_t(15);
+        if (a1 > a0)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0),
+                       "r"((unsigned)(a1 - a0))
+                       : "memory");
+      }
       bool bad = false;
+#pragma unroll 4
       for (int i = lane; i < n; i += 32) {
         const int src = orig_index(perm, gb, i);
 #pragma unroll

@@ -218,3 +218,20 @@ def test_capacity_and_tolerance_checks():
         m.merge(cells, pos, mom, w, -0.1, 0.1)
     assert ei.value.code == binding.PMA_ERR_INVALID_ARG
     m.close()
+
+
+def test_mixed_verbatim_copies_are_exact_for_special_values():
+    # one-particle sets and pass-through cells are copied verbatim: the float32
+    # -> float64 widening must be exact for zeros, subnormals and extremes
+    vals = np.array([0.0, -0.0, 1e-40, -3e-39, 1.4e-45, 3.3e38, -2.5e-38, 1.17549435e-38],
+                    dtype=np.float32)
+    n = vals.size
+    p = synth.Particles("special", 1, 3, n, (1.0, 1.0, 1.0), 0.1, 0.1, 0,
+                        np.arange(n, dtype=np.int32), (np.arange(n) + 0.5)[None, :].astype(np.float32),
+                        np.stack([vals, vals[::-1], vals]).astype(np.float32),
+                        np.linspace(0.5, 2.0, n).astype(np.float32))
+    g = run_gpu(p, "mixed")
+    assert g["count"] == n
+    np.testing.assert_array_equal(g["mom"], p.mom.astype(np.float64))
+    assert np.array_equal(np.signbit(g["mom"]), np.signbit(p.mom))
+    np.testing.assert_array_equal(g["w"], p.w.astype(np.float64))
