@@ -213,14 +213,13 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   while (cap > 64 && unit_smem(h->mixed, h->D, cap) + 4096 > (size_t)smem_optin) cap -= 64;
   h->cap = cap;
   h->unit_grid = h->sms;
-  // warp-per-cell class: cells up to cap_w particles, one warp each
+  // warp-team class: cells up to cap_w particles, one team of warps each
   const size_t smem_sm = (size_t)smem_optin + 1024;
   h->cap_w = 1024;
+  while (h->cap_w > 128 && warp_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
+    h->cap_w -= 64;
   h->warps_per_cta = 4;
-  while (h->warps_per_cta > 1 &&
-         (size_t)h->warps_per_cta * warp_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
-    --h->warps_per_cta;
-  const size_t cta_smem = (size_t)h->warps_per_cta * warp_smem(h->mixed, h->D, h->cap_w);
+  const size_t cta_smem = warp_smem(h->mixed, h->D, h->cap_w);
   h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (cta_smem + 1024)));
   const int64_t N = std::max<int64_t>(cfg->capacity, 1);
   const int64_t C = cfg->n_cells;

@@ -69,7 +69,7 @@ template <typename T, int D>
 __host__ __device__ inline size_t warp_region_bytes(int cap) {
   size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
-  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + kClasses * sizeof(int);
+  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 4) * sizeof(int);
   return (b + 15) & ~size_t(15);
 }
 
@@ -100,19 +100,15 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
     set_error(P.err, kErrInternal);
 }
 
-// one round of class c >= 1: 32/G subsets, G lanes each
+// one round of class c >= 1 for this warp: kw <= 32/G subsets (stack
+// entries base, base - 1, ...), G lanes each
 template <typename T, int D>
 __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                            int64_t gb, int c, int lane, Counters &cnt) {
-  const int lg = c - 1, G = 1 << lg, per = 32 >> lg;
-  const int avail = S.top[c];
-  const int k = min(avail, per);
+                            int64_t gb, int c, int lane, Counters &cnt, int kw, int base) {
+  const int lg = c - 1, G = 1 << lg;
   const int gid = lane >> lg, gl = lane & (G - 1);
-  const bool act = gid < k;
-  uint32_t rec = act ? S.stk[c][avail - 1 - gid] : 0u;
-  __syncwarp();
-  if (lane == 0) S.top[c] = avail - k;
-  __syncwarp();
+  const bool act = gid < kw;
+  const uint32_t rec = act ? S.stk[c][base - gid] : 0u;
   const int b = rec & 2047, m = act ? (int)((rec >> 11) & 4095) : 0, par = (rec >> 23) & 1;
 
   // Steps 1-2: moments about the set's first particle
@@ -201,17 +197,13 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   __syncwarp();
 }
 
-// one round of two-particle sets, one per lane
+// one round of two-particle sets for this warp: kw <= 32 of them (stack
+// entries base, base - 1, ...), one per lane
 template <typename T, int D>
 __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                           int64_t gb, int lane, Counters &cnt) {
-  const int avail = S.top[0];
-  const int k = min(avail, 32);
-  const bool act = lane < k;
-  const uint32_t rec = act ? S.stk[0][avail - 1 - lane] : 0u;
-  __syncwarp();
-  if (lane == 0) S.top[0] = avail - k;
-  __syncwarp();
+                           int64_t gb, int lane, Counters &cnt, int kw, int base) {
+  const bool act = lane < kw;
+  const uint32_t rec = act ? S.stk[0][base - lane] : 0u;
   if (!act) return;
   const int b = rec & 2047, par = (rec >> 23) & 1;
   const int ja = S.idx[par][b], jb = S.idx[par][b + 1];
@@ -264,14 +256,23 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
 
 // --------------------------------------------------------------- kernel
 
+constexpr int kTeam = 2;         // warps sharing one cell
+constexpr int kTeamsPerCta = 2;  // CTA of kTeam * kTeamsPerCta warps
+
+__device__ __forceinline__ void team_sync(int team) {
+  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(32 * kTeam) : "memory");
+}
+
 template <typename T, int D>
-__global__ void __launch_bounds__(128) warp_kernel(Problem P) {
+__global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int team = warp / kTeam, wt = warp % kTeam, tt = threadIdx.x % (32 * kTeam);
   const int cap = P.cap_w;
   WarpTile<T, D> S;
+  int *ctl;
   {
-    unsigned char *base = smem_raw + (size_t)warp * warp_region_bytes<T, D>(cap);
+    unsigned char *base = smem_raw + (size_t)team * warp_region_bytes<T, D>(cap);
     S.data = reinterpret_cast<T *>(base);
     S.idx[0] = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
     S.idx[1] = S.idx[0] + cap;
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
       st += class_capacity(c, cap);
     }
     S.top = reinterpret_cast<int *>(st);
+    ctl = S.top + kClasses;
     S.cap = cap;
   }
   const int32_t *perm = (*P.unsorted == 0) ? nullptr : P.perm;
@@ -292,9 +294,10 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
   unsigned long long merged = 0, passed = 0;
 
   for (;;) {
-    int c0 = 0;
-    if (lane == 0) c0 = atomicAdd(P.warp_next, kWarpChunk);
-    c0 = __shfl_sync(0xffffffffu, c0, 0);
+    if (tt == 0) ctl[0] = atomicAdd(P.warp_next, kWarpChunk);
+    team_sync(team);
+    const int c0 = ctl[0];
+    team_sync(team);
     if (c0 >= count) break;
     const int c1 = min(c0 + kWarpChunk, count);
     for (int t = c0; t < c1; ++t) {
@@ -303,17 +306,17 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
       const int n = P.cell_begin[cell + 1] - (int)gb;
       if (n <= P.n_min || n == 1) {
         // Sec. 3 "Input": cells with at most N_min particles are not merged
-        for (int i = lane; i < n; i += 32) emit_single(P, perm, gb, i, i);
+        for (int i = tt; i < n; i += 32 * kTeam) emit_single(P, perm, gb, i, i);
         passed += 1;
         continue;
       }
       merged += 1;
-      if (t + 1 < c1 && !perm && lane < D + 1) {
+      if (t + 1 < c1 && !perm && tt < D + 1) {
         // the next cell of this chunk: pull its columns into L2 meanwhile
         const int nc = P.warp_list[t + 1];
         const int64_t nb = P.cell_begin[nc], ne = P.cell_begin[nc + 1];
         const size_t es = sizeof(T);
-        const char *col = static_cast<const char *>(lane < D ? P.q[lane] : P.w);
+        const char *col = static_cast<const char *>(tt < D ? P.q[tt] : P.w);
         // the 16-byte-aligned part of the range only: never outside the array
         const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nb * es) + 15) & ~uintptr_t(15);
         const uintptr_t a1 = (reinterpret_cast<uintptr_t>(col + ne * es)) & ~uintptr_t(15);
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
       }
       bool bad = false;
 #pragma unroll 4
-      for (int i = lane; i < n; i += 32) {
+      for (int i = tt; i < n; i += 32 * kTeam) {
         const int src = orig_index(perm, gb, i);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
@@ -338,24 +341,36 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
         S.idx[0][i] = (uint16_t)i;
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
-      if (lane < kClasses) S.top[lane] = 0;
-      __syncwarp();
-      if (lane == 0) {
+      if (tt < kClasses) S.top[tt] = 0;
+      team_sync(team);
+      if (tt == 0) {
         const int c = size_class(n);
         S.stk[c][0] = pack_rec(0, n, 0);
         S.top[c] = 1;
       }
-      __syncwarp();
+      // rounds: the team pops up to kTeam * 32/G subsets of the largest
+      // non-empty class; warp wt takes the wt-th share
       for (;;) {
+        team_sync(team);
         int c = -1;
 #pragma unroll
         for (int k = kClasses - 1; k >= 0; --k)
           if (c < 0 && S.top[k] > 0) c = k;
         if (c < 0) break;
-        if (c == 0)
-          pair_round<T, D>(P, S, perm, gb, lane, cnt);
-        else
-          group_round<T, D>(P, S, perm, gb, c, lane, cnt);
+        const int per = (c == 0) ? 32 : (32 >> (c - 1));
+        const int avail = S.top[c];
+        const int k = min(avail, kTeam * per);
+        const int kw = max(0, min(per, k - wt * per));
+        const int base = avail - 1 - wt * per;
+        team_sync(team);
+        if (tt == 0) S.top[c] = avail - k;
+        team_sync(team);
+        if (kw > 0) {
+          if (c == 0)
+            pair_round<T, D>(P, S, perm, gb, lane, cnt, kw, base);
+          else
+            group_round<T, D>(P, S, perm, gb, c, lane, cnt, kw, base);
+        }
         __syncwarp();
       }
     }
@@ -372,8 +387,8 @@ __global__ void __launch_bounds__(128) warp_kernel(Problem P) {
     if (cnt.depth) atomicAdd(&P.stats[kStDepth], cnt.depth);
     if (cnt.splits) atomicAdd(&P.stats[kStSplits], cnt.splits);
     if (cnt.degenerate) atomicAdd(&P.stats[kStDegenerate], cnt.degenerate);
-    if (merged) atomicAdd(&P.stats[kStCellsMerged], merged);
-    if (passed) atomicAdd(&P.stats[kStCellsPass], passed);
+    if (wt == 0 && merged) atomicAdd(&P.stats[kStCellsMerged], merged);
+    if (wt == 0 && passed) atomicAdd(&P.stats[kStCellsPass], passed);
   }
 }
 
@@ -390,37 +405,39 @@ static size_t warp_smem_t(int D, int cap) {
   }
 }
 
+// shared memory of one CTA (kTeamsPerCta cells)
 size_t warp_smem(int mixed, int D, int cap_w) {
-  return mixed ? warp_smem_t<float>(D, cap_w) : warp_smem_t<double>(D, cap_w);
+  return kTeamsPerCta * (mixed ? warp_smem_t<float>(D, cap_w) : warp_smem_t<double>(D, cap_w));
 }
 
 template <typename T, int D>
-static cudaError_t launch_warps_t(const Problem &P, int wpc, int grid, cudaStream_t st) {
+static cudaError_t launch_warps_t(const Problem &P, int grid, cudaStream_t st) {
   if (P.cap_w > kMaxCapW) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)wpc * warp_region_bytes<T, D>(P.cap_w);
+  const size_t smem = (size_t)kTeamsPerCta * warp_region_bytes<T, D>(P.cap_w);
   cudaError_t e = cudaFuncSetAttribute(warp_kernel<T, D>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  warp_kernel<T, D><<<grid, 32 * wpc, smem, st>>>(P);
+  warp_kernel<T, D><<<grid, 32 * kTeam * kTeamsPerCta, smem, st>>>(P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_warps(const Problem &P, int mixed, int wpc, int grid, cudaStream_t st) {
+  (void)wpc;
   if (mixed) {
     switch (P.D) {
-      case 2: return launch_warps_t<float, 2>(P, wpc, grid, st);
-      case 3: return launch_warps_t<float, 3>(P, wpc, grid, st);
-      case 4: return launch_warps_t<float, 4>(P, wpc, grid, st);
-      case 5: return launch_warps_t<float, 5>(P, wpc, grid, st);
-      default: return launch_warps_t<float, 6>(P, wpc, grid, st);
+      case 2: return launch_warps_t<float, 2>(P, grid, st);
+      case 3: return launch_warps_t<float, 3>(P, grid, st);
+      case 4: return launch_warps_t<float, 4>(P, grid, st);
+      case 5: return launch_warps_t<float, 5>(P, grid, st);
+      default: return launch_warps_t<float, 6>(P, grid, st);
     }
   }
   switch (P.D) {
-    case 2: return launch_warps_t<double, 2>(P, wpc, grid, st);
-    case 3: return launch_warps_t<double, 3>(P, wpc, grid, st);
-    case 4: return launch_warps_t<double, 4>(P, wpc, grid, st);
-    case 5: return launch_warps_t<double, 5>(P, wpc, grid, st);
-    default: return launch_warps_t<double, 6>(P, wpc, grid, st);
+    case 2: return launch_warps_t<double, 2>(P, grid, st);
+    case 3: return launch_warps_t<double, 3>(P, grid, st);
+    case 4: return launch_warps_t<double, 4>(P, grid, st);
+    case 5: return launch_warps_t<double, 5>(P, grid, st);
+    default: return launch_warps_t<double, 6>(P, grid, st);
   }
 }
 
