@@ -256,8 +256,8 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
 
 // --------------------------------------------------------------- kernel
 
-constexpr int kTeam = 2;         // warps sharing one cell
-constexpr int kTeamsPerCta = 2;  // CTA of kTeam * kTeamsPerCta warps
+constexpr int kTeam = 4;         // warps sharing one cell
+constexpr int kTeamsPerCta = 1;  // CTA of kTeam * kTeamsPerCta warps
 
 __device__ __forceinline__ void team_sync(int team) {
   asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(32 * kTeam) : "memory");
