@@ -76,6 +76,7 @@ struct pma_handle {
   int32_t *counts = nullptr, *cell_begin = nullptr, *fill = nullptr;
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
   int32_t *warp_list = nullptr, *block_list = nullptr;
+  void *fin = nullptr;  // staging: D + 1 columns of capacity entries
   uint8_t *head = nullptr;
   unsigned long long *bin_status = nullptr, *emit_status = nullptr;
   int4 *pieces = nullptr;
@@ -118,7 +119,7 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->bin_status, h->emit_status,
-                  h->pieces, h->ctl, h->warp_list, h->block_list, h->stage.cells, h->stage.w, h->stage.out_cell,
+                  h->pieces, h->ctl, h->warp_list, h->block_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -232,6 +233,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
+            cudaMalloc(&h->fin, (size_t)N * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->emit_status, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
@@ -338,6 +340,11 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   for (int a = 0; a < h->cfg.dp; ++a) P.q[h->cfg.dx + a] = mom[a];
   P.w = weights;
   P.cells = cells;
+  {
+    const size_t es = h->mixed ? 4 : 8;
+    for (int l = 0; l <= h->D; ++l)
+      P.fin[l] = static_cast<char *>(h->fin) + (size_t)l * h->capacity * es;
+  }
   P.cell_begin = h->cell_begin;
   P.perm = h->perm;
   P.head = h->head;
@@ -380,8 +387,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.head = h->head;
   m.perm_final = h->perm_final;
   m.cells = cells;
-  for (int l = 0; l < h->D; ++l) m.q[l] = P.q[l];
-  m.w = weights;
+  m.unsorted = &h->ctl->unsorted;
+  for (int l = 0; l <= h->D; ++l) m.fin[l] = P.fin[l];
   m.out_cell = out->cell;
   for (int a = 0; a < 3; ++a) {
     m.out_pos[a] = out->pos[a];

@@ -83,81 +83,54 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   const long long prefix = s_prefix;
   const int32_t *__restrict__ perm_final = a.perm_final;
   const int32_t *__restrict__ cells = a.cells;
-  const T *__restrict__ win = static_cast<const T *>(a.w);
+  const bool sorted = *a.unsorted == 0;
+  const int D = a.dx + a.dp;
   bool bad = false, internal = false;
-  // positions in strided order (consecutive threads, consecutive positions),
-  // in batches whose loads are issued before their stores
-  constexpr int kB = 4;
-  for (int jb = 0; jb < kEmitChunk; jb += kB) {
-    int orig[kB], hh[kB];
-    long long slot[kB];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int off = (jb + u) * kEmitThreads + tid;
-      const int64_t p = t0 + off;
-      orig[u] = -1;
-      hh[u] = 0;
-      slot[u] = 0;
-      if (p < a.n) {
-        const int ch = off / kEmitChunk, in = off % kEmitChunk;
-        const unsigned m = s_mask[ch];
-        slot[u] = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
-        orig[u] = perm_final[p];
-        hh[u] = s_head[off];
-        if ((unsigned)orig[u] >= (unsigned)a.n) {
-          // a position left unwritten by an earlier failure: never follow it
-          internal = true;
-          orig[u] = -1;
-          hh[u] = 0;
-        }
-      }
+  // positions in strided order: consecutive threads, consecutive positions;
+  // staged values, final positions and output slots all advance together
+#pragma unroll 4
+  for (int j = 0; j < kEmitChunk; ++j) {
+    const int off = j * kEmitThreads + tid;
+    const int64_t p = t0 + off;
+    if (p >= a.n) break;
+    const int ch = off / kEmitChunk, in = off % kEmitChunk;
+    const unsigned m = s_mask[ch];
+    const long long slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
+    const int orig = perm_final[p];
+    if ((unsigned)orig >= (unsigned)a.n) {
+      // a position left unwritten by an earlier failure: never follow it
+      internal = true;
+      continue;
     }
-    T xs[kB][kMaxD];
-    T ws[kB];
-    int cs[kB];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      cs[u] = 0;
-      ws[u] = T(1);
-#pragma unroll
-      for (int l = 0; l < kMaxD; ++l) xs[u][l] = T(0);
-      if (hh[u]) cs[u] = cells[orig[u]];
-      if (hh[u] == kHeadSingle) {
-#pragma unroll
-        for (int l = 0; l < kMaxD; ++l)
-          if (l < a.dx + a.dp) xs[u][l] = static_cast<const T *>(a.q[l])[orig[u]];
-        ws[u] = win[orig[u]];
+    if (a.out_index) a.out_index[orig] = (int32_t)slot;
+    const int h = s_head[off];
+    if (!h) continue;
+    a.out_cell[slot] = cells[sorted ? p : (int64_t)orig];
+    if (h == kHeadSingle) {
+      // one-particle set: the particle itself (Step 7)
+      for (int l = 0; l < a.dx; ++l) {
+        const T x = static_cast<const T *>(a.fin[l])[p];
+        bad |= !isfinite(x);
+        static_cast<T *>(a.out_pos[l])[slot] = x;
       }
-    }
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      if (orig[u] < 0) continue;
-      if (a.out_index) a.out_index[orig[u]] = (int32_t)slot[u];
-      if (!hh[u]) continue;
-      a.out_cell[slot[u]] = cs[u];
-      if (hh[u] == kHeadSingle) {
-        // one-particle set: the particle itself (Step 7)
-        for (int l = 0; l < a.dx; ++l) {
-          bad |= !isfinite(xs[u][l]);
-          static_cast<T *>(a.out_pos[l])[slot[u]] = xs[u][l];
-        }
-        for (int l = 0; l < a.dp; ++l) {
-          bad |= !isfinite(xs[u][a.dx + l]);
-          a.out_mom[l][slot[u]] = to_f64<T>(xs[u][a.dx + l]);
-        }
-        bad |= !(ws[u] > T(0)) || !isfinite(ws[u]);
-        a.out_w[slot[u]] = to_f64<T>(ws[u]);
-      } else {
-        // merged set: summed below, densely, by the whole CTA
-        const int k = atomicAdd(&s_nmerged, 1);
-        s_merged[k] = make_int2((jb + u) * kEmitThreads + tid, (int)slot[u]);
+      for (int l = 0; l < a.dp; ++l) {
+        const T x = static_cast<const T *>(a.fin[a.dx + l])[p];
+        bad |= !isfinite(x);
+        a.out_mom[l][slot] = to_f64<T>(x);
       }
+      const T w = static_cast<const T *>(a.fin[D])[p];
+      bad |= !(w > T(0)) || !isfinite(w);
+      a.out_w[slot] = to_f64<T>(w);
+    } else {
+      // merged set: summed below, densely, by the whole CTA
+      const int k = atomicAdd(&s_nmerged, 1);
+      s_merged[k] = make_int2(off, (int)slot);
     }
   }
   __syncthreads();
-  // merged sets of this tile: members are the positions up to the next head;
-  // W, W X and W P are FP64 sums (a product of two floats is exact in FP64)
-  const int D = a.dx + a.dp;
+  // merged sets of this tile: members are the staged positions up to the next
+  // head; W, W X and W P are FP64 sums (a product of two floats is exact in
+  // FP64)
   for (int k = tid; k < s_nmerged; k += kEmitThreads) {
     const int64_t p = t0 + s_merged[k].x;
     const long long slot = s_merged[k].y;
@@ -166,16 +139,11 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
     for (int64_t r = p; r < a.n; ++r) {
       if (r > p && a.head[r]) break;
-      const int o = perm_final[r];
-      if ((unsigned)o >= (unsigned)a.n) {
-        internal = true;
-        break;
-      }
-      const double w = to_f64<T>(win[o]);
+      const double w = to_f64<T>(static_cast<const T *>(a.fin[D])[r]);
       W += w;
 #pragma unroll
       for (int l = 0; l < kMaxD; ++l)
-        if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.q[l])[o]), S1[l]);
+        if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.fin[l])[r]), S1[l]);
     }
     const double inv = 1.0 / W;
     a.out_w[slot] = W;

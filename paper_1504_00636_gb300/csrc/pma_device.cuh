@@ -62,6 +62,8 @@ struct Problem {
   int32_t *perm;          // sorted position -> input index (workspace)
   uint8_t *head;          // [N] head byte per final position
   int32_t *perm_final;    // [N] input index at each final position
+  void *fin[kMaxD + 1];   // [D + 1][N] coordinates and weight in final order,
+                          // or all null (then the emit step gathers)
   unsigned *err;          // device status word
   unsigned long long *stats;
   // big cells: cells above `cap` are cut in global memory first

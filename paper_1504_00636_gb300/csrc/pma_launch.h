@@ -49,8 +49,8 @@ struct EmitArgs {
   const uint8_t *head;
   const int32_t *perm_final;
   const int32_t *cells;
-  const void *q[kMaxD];
-  const void *w;
+  const int32_t *unsorted;  // device flag: cell ids of final positions are cells[p] when 0
+  const void *fin[kMaxD + 1];  // staged coordinates and weight in final order
   int32_t *out_cell;
   void *out_pos[3];
   double *out_mom[3];

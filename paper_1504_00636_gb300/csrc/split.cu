@@ -37,6 +37,24 @@ struct Tile {
   }
 };
 
+// particle j of buffer `par`, staged at final position gp (when staging is on)
+template <typename T, int D>
+__device__ __forceinline__ void stage_tile(const Problem &P, const Tile<T, D> &S, int par,
+                                           int64_t gp, int j) {
+  if (!P.fin[0]) return;
+#pragma unroll
+  for (int l = 0; l <= D; ++l) static_cast<T *>(P.fin[l])[gp] = S.col(par, l)[j];
+}
+
+// input particle src, staged at final position gp (when staging is on)
+template <typename T, int D>
+__device__ __forceinline__ void stage_global(const Problem &P, int64_t gp, int src) {
+  if (!P.fin[0]) return;
+#pragma unroll
+  for (int l = 0; l < D; ++l) static_cast<T *>(P.fin[l])[gp] = StoreOf<T>::load(P.q[l], src);
+  static_cast<T *>(P.fin[D])[gp] = StoreOf<T>::load(P.w, src);
+}
+
 template <typename T, int D>
 __host__ __device__ inline size_t unit_smem_bytes(int cap) {
   size_t v = (size_t)2 * (D + 1) * cap * sizeof(T);
@@ -57,6 +75,7 @@ __device__ void emit_leaf_warp(const Problem &P, const Tile<T, D> &S, const int3
   for (int j = b + lane; j < e; j += 32) {
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
+    stage_tile<T, D>(P, S, par, gb + j, j);
   }
 }
 
@@ -69,6 +88,7 @@ __device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const in
   for (int j = b; j < e; ++j) {
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
+    stage_tile<T, D>(P, S, par, gb + j, j);
   }
 }
 
@@ -140,6 +160,7 @@ __device__ void warp_split(const Problem &P, const Tile<T, D> &S, const int32_t 
       if (n == 1) {
         P.perm_final[gb + ch[h].b] = orig_index(perm, gb, S.id[np][ch[h].b]);
         P.head[gb + ch[h].b] = kHeadSingle;
+        stage_tile<T, D>(P, S, np, gb + ch[h].b, ch[h].b);
         atomicAdd(&st[kStLeaves], 1ull);
         atomicAdd(&st[kStDepth], (unsigned long long)ch[h].depth);
       } else if (n <= kSmall) {
@@ -169,6 +190,7 @@ __device__ void thread_finish(const Problem &P, const Tile<T, D> &S, const int32
     if (e - b == 1) {
       P.perm_final[gb + b] = orig_index(perm, gb, S.id[par][b]);
       P.head[gb + b] = kHeadSingle;
+      stage_tile<T, D>(P, S, par, gb + b, b);
       cnt[0] += 1;
       cnt[1] += it.depth;
       continue;
@@ -260,8 +282,10 @@ __global__ void __launch_bounds__(256) unit_kernel(Problem P, int mode) {
       if (n == 0) continue;
       if (n <= P.n_min || n == 1) {
         for (int i = tid; i < n; i += blockDim.x) {
-          P.perm_final[gb + i] = orig_index(perm, gb, i);
+          const int src = orig_index(perm, gb, i);
+          P.perm_final[gb + i] = src;
           P.head[gb + i] = kHeadSingle;
+          stage_global<T, D>(P, gb + i, src);
         }
         if (tid == 0) s_st[kStCellsPass] += 1;
         continue;
@@ -462,6 +486,7 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
         for (int64_t i = b + tid; i < e; i += blockDim.x) {
           P.perm_final[i] = P.perm[i];
           P.head[i] = (i == b) ? ((e - b == 1) ? kHeadSingle : kHeadMerged) : (uint8_t)0;
+          stage_global<T, D>(P, i, P.perm[i]);
         }
         if (tid == 0) {
           atomicAdd(&P.stats[kStLeaves], 1ull);

@@ -77,10 +77,20 @@ struct Counters {
   unsigned long long leaves, depth, splits, degenerate;
 };
 
-__device__ __forceinline__ void emit_single(const Problem &P, const int32_t *perm, int64_t gb,
-                                            int pos, int j) {
+// particle j of the tile, staged at final position gp
+template <typename T, int D>
+__device__ __forceinline__ void stage(const Problem &P, const WarpTile<T, D> &S, int64_t gp,
+                                      int j) {
+#pragma unroll
+  for (int l = 0; l <= D; ++l) static_cast<T *>(P.fin[l])[gp] = S.col(l)[j];
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void emit_single(const Problem &P, const WarpTile<T, D> &S,
+                                            const int32_t *perm, int64_t gb, int pos, int j) {
   P.perm_final[gb + pos] = orig_index(perm, gb, j);
   P.head[gb + pos] = kHeadSingle;
+  stage<T, D>(P, S, gb + pos, j);
 }
 
 template <typename T, int D>
@@ -88,7 +98,7 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
                                            const int32_t *perm, int64_t gb, int b, int m,
                                            int par, Counters &cnt) {
   if (m == 1) {
-    emit_single(P, perm, gb, b, S.idx[par][b]);
+    emit_single<T, D>(P, S, perm, gb, b, S.idx[par][b]);
     cnt.leaves += 1;
     return;
   }
@@ -179,8 +189,10 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   if (final_set) {
     const uint8_t h = (m == 1) ? kHeadSingle : kHeadMerged;
     for (int i = gl; i < m; i += G) {
-      P.perm_final[gb + b + i] = orig_index(perm, gb, S.idx[epar][b + i]);
+      const int j = S.idx[epar][b + i];
+      P.perm_final[gb + b + i] = orig_index(perm, gb, j);
       P.head[gb + b + i] = (i == 0) ? h : (uint8_t)0;
+      stage<T, D>(P, S, gb + b + i, j);
     }
   }
   if (gl == 0 && act) {
@@ -241,6 +253,8 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
   }
   P.perm_final[gb + b] = orig_index(perm, gb, first);
   P.perm_final[gb + b + 1] = orig_index(perm, gb, second);
+  stage<T, D>(P, S, gb + b, first);
+  stage<T, D>(P, S, gb + b + 1, second);
   if (merged) {
     P.head[gb + b] = kHeadMerged;
     P.head[gb + b + 1] = 0;
@@ -306,7 +320,15 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
       const int n = P.cell_begin[cell + 1] - (int)gb;
       if (n <= P.n_min || n == 1) {
         // Sec. 3 "Input": cells with at most N_min particles are not merged
-        for (int i = tt; i < n; i += 32 * kTeam) emit_single(P, perm, gb, i, i);
+        for (int i = tt; i < n; i += 32 * kTeam) {
+          const int src = orig_index(perm, gb, i);
+          P.perm_final[gb + i] = src;
+          P.head[gb + i] = kHeadSingle;
+#pragma unroll
+          for (int l = 0; l < D; ++l)
+            static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
+          static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+        }
         passed += 1;
         continue;
       }
