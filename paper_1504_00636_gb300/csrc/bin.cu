@@ -69,7 +69,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
   }
   int total;
   int ex = block_exclusive_scan(sum, s_warp, &total);
-  if (threadIdx.x == 0) s_prefix = tile_exclusive_prefix(a.scan_status, tile, total, a.err);
+  if (threadIdx.x < 32) {
+    const long long pre = warp_exclusive_prefix(a.scan_status, tile, total, a.err);
+    if (threadIdx.x == 0) s_prefix = pre;
+  }
   __syncthreads();
   long long run = s_prefix + ex;
 #pragma unroll

@@ -71,12 +71,14 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   const int ex = block_exclusive_scan(__popc(mask), s_warp, &total);
   s_mask[tid] = (unsigned short)mask;
   s_chunk[tid] = ex;
-  if (tid == 0) {
-    const long long pre = tile_exclusive_prefix(a.scan_status, tile, total, a.err);
-    s_prefix = pre;
-    if (tile == a.tiles - 1) {
-      if (a.out_count) *a.out_count = pre + total;
-      if (a.out_count2) *a.out_count2 = pre + total;
+  if (tid < 32) {
+    const long long pre = warp_exclusive_prefix(a.scan_status, tile, total, a.err);
+    if (tid == 0) {
+      s_prefix = pre;
+      if (tile == a.tiles - 1) {
+        if (a.out_count) *a.out_count = pre + total;
+        if (a.out_count2) *a.out_count2 = pre + total;
+      }
     }
   }
   __syncthreads();

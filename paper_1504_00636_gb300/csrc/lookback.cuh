@@ -65,6 +65,49 @@ __device__ inline long long tile_exclusive_prefix(unsigned long long *status, in
   return prefix;
 }
 
+// Warp-wide version: called by all 32 lanes of one warp; examines 32
+// predecessors per step.  Returns the exclusive prefix of `tile` in every lane.
+__device__ inline long long warp_exclusive_prefix(unsigned long long *status, int tile,
+                                                  long long aggregate, unsigned *err) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
+    return 0;
+  }
+  if (lane == 0) st_release_u64(&status[tile], kFlagAgg | (unsigned long long)aggregate);
+  long long prefix = 0;
+  int t = tile - 1;  // newest predecessor not yet summed
+  unsigned long long t0 = 0;
+  while (t >= 0) {
+    const int q = t - lane;
+    unsigned long long sv = q >= 0 ? ld_acquire_u64(&status[q]) : (kFlagInc | 0ull);
+    const unsigned long long f = sv >> 62;
+    // lanes up to the nearest inclusive prefix must all be ready
+    const unsigned inc = __ballot_sync(0xffffffffu, f == 2);
+    const int stop = inc ? (__ffs(inc) - 1) : 31;  // lane holding the inclusive (or last)
+    const unsigned notready = __ballot_sync(0xffffffffu, f == 0) & ((2u << stop) - 1u);
+    if (notready) {
+      unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    long long v = (lane <= stop) ? (long long)(sv & kValMask) : 0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    prefix += v;
+    if (inc) break;
+    t -= 32;
+  }
+  if (lane == 0) st_release_u64(&status[tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+  return prefix;
+}
+
 // exclusive scan of one int per thread across the CTA (blockDim <= 1024);
 // `warp_sums` holds 32 ints of shared memory; returns the block total in *total
 __device__ inline int block_exclusive_scan(int v, int *warp_sums, int *total) {
