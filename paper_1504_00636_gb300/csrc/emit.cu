@@ -12,7 +12,7 @@
 namespace pma {
 
 constexpr int kEmitThreads = 256;
-constexpr int kEmitChunk = 16;  // consecutive positions per chunk
+constexpr int kEmitChunk = 4;  // consecutive positions per chunk
 constexpr int kEmitTile = kEmitThreads * kEmitChunk;
 
 int emit_tiles_for(int64_t n) { return (int)((n + kEmitTile - 1) / kEmitTile); }
@@ -46,27 +46,20 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   __syncthreads();
   const int tile = s_tile;
   const int64_t t0 = (int64_t)tile * kEmitTile;
-  // heads of my chunk of 16 consecutive positions
+  // heads of my chunk of 4 consecutive positions
   const int64_t c0 = t0 + (int64_t)tid * kEmitChunk;
-  unsigned mask = 0;
-  uint4 hv = make_uint4(0u, 0u, 0u, 0u);
+  unsigned hw = 0;
   if (c0 + kEmitChunk <= a.n) {
-    hv = *reinterpret_cast<const uint4 *>(a.head + c0);
+    hw = *reinterpret_cast<const unsigned *>(a.head + c0);
   } else {
-    uint8_t hb[kEmitChunk];
-    for (int j = 0; j < kEmitChunk; ++j) hb[j] = (c0 + j < a.n) ? a.head[c0 + j] : (uint8_t)0;
-    hv.x = hb[0] | (hb[1] << 8) | (hb[2] << 16) | ((unsigned)hb[3] << 24);
-    hv.y = hb[4] | (hb[5] << 8) | (hb[6] << 16) | ((unsigned)hb[7] << 24);
-    hv.z = hb[8] | (hb[9] << 8) | (hb[10] << 16) | ((unsigned)hb[11] << 24);
-    hv.w = hb[12] | (hb[13] << 8) | (hb[14] << 16) | ((unsigned)hb[15] << 24);
+    for (int j = 0; j < kEmitChunk; ++j)
+      if (c0 + j < a.n) hw |= (unsigned)a.head[c0 + j] << (8 * j);
   }
-  {
-    const unsigned wv[4] = {hv.x, hv.y, hv.z, hv.w};
+  unsigned mask = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if ((wv[j >> 2] >> (8 * (j & 3))) & 0xffu) mask |= 1u << j;
-    *reinterpret_cast<uint4 *>(s_head + tid * kEmitChunk) = hv;
-  }
+  for (int j = 0; j < kEmitChunk; ++j)
+    if ((hw >> (8 * j)) & 0xffu) mask |= 1u << j;
+  reinterpret_cast<unsigned *>(s_head)[tid] = hw;
   int total;
   const int ex = block_exclusive_scan(__popc(mask), s_warp, &total);
   s_mask[tid] = (unsigned short)mask;
@@ -89,44 +82,64 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   const int D = a.dx + a.dp;
   bool bad = false, internal = false;
   // positions in strided order: consecutive threads, consecutive positions;
-  // staged values, final positions and output slots all advance together
-#pragma unroll 4
+  // all loads of a thread's positions are issued before its stores
+  int orig[kEmitChunk], hh[kEmitChunk], cc[kEmitChunk];
+  long long slot[kEmitChunk];
+  T xv[kEmitChunk][kMaxD + 1];
+#pragma unroll
   for (int j = 0; j < kEmitChunk; ++j) {
     const int off = j * kEmitThreads + tid;
     const int64_t p = t0 + off;
-    if (p >= a.n) break;
-    const int ch = off / kEmitChunk, in = off % kEmitChunk;
-    const unsigned m = s_mask[ch];
-    const long long slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
-    const int orig = perm_final[p];
-    if ((unsigned)orig >= (unsigned)a.n) {
+    orig[j] = -1;
+    hh[j] = -1;  // beyond n
+    cc[j] = 0;
+    slot[j] = 0;
+#pragma unroll
+    for (int l = 0; l <= kMaxD; ++l) xv[j][l] = T(1);
+    if (p < a.n) {
+      const int ch = off / kEmitChunk, in = off % kEmitChunk;
+      const unsigned m = s_mask[ch];
+      slot[j] = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
+      orig[j] = perm_final[p];
+      hh[j] = s_head[off];
+      if (hh[j]) {
+        cc[j] = cells[sorted ? p : (int64_t)max(orig[j], 0)];
+        if (hh[j] == kHeadSingle) {
+#pragma unroll
+          for (int l = 0; l <= kMaxD; ++l)
+            if (l <= D) xv[j][l] = static_cast<const T *>(a.fin[l])[p];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kEmitChunk; ++j) {
+    if (hh[j] < 0) continue;
+    if ((unsigned)orig[j] >= (unsigned)a.n) {
       // a position left unwritten by an earlier failure: never follow it
       internal = true;
       continue;
     }
-    if (a.out_index) a.out_index[orig] = (int32_t)slot;
-    const int h = s_head[off];
-    if (!h) continue;
-    a.out_cell[slot] = cells[sorted ? p : (int64_t)orig];
-    if (h == kHeadSingle) {
+    if (a.out_index) a.out_index[orig[j]] = (int32_t)slot[j];
+    if (!hh[j]) continue;
+    a.out_cell[slot[j]] = cc[j];
+    if (hh[j] == kHeadSingle) {
       // one-particle set: the particle itself (Step 7)
       for (int l = 0; l < a.dx; ++l) {
-        const T x = static_cast<const T *>(a.fin[l])[p];
-        bad |= !isfinite(x);
-        static_cast<T *>(a.out_pos[l])[slot] = x;
+        bad |= !isfinite(xv[j][l]);
+        static_cast<T *>(a.out_pos[l])[slot[j]] = xv[j][l];
       }
       for (int l = 0; l < a.dp; ++l) {
-        const T x = static_cast<const T *>(a.fin[a.dx + l])[p];
-        bad |= !isfinite(x);
-        a.out_mom[l][slot] = to_f64<T>(x);
+        bad |= !isfinite(xv[j][a.dx + l]);
+        a.out_mom[l][slot[j]] = to_f64<T>(xv[j][a.dx + l]);
       }
-      const T w = static_cast<const T *>(a.fin[D])[p];
+      const T w = xv[j][D];
       bad |= !(w > T(0)) || !isfinite(w);
-      a.out_w[slot] = to_f64<T>(w);
+      a.out_w[slot[j]] = to_f64<T>(w);
     } else {
       // merged set: summed below, densely, by the whole CTA
       const int k = atomicAdd(&s_nmerged, 1);
-      s_merged[k] = make_int2(off, (int)slot);
+      s_merged[k] = make_int2(j * kEmitThreads + tid, (int)slot[j]);
     }
   }
   __syncthreads();
