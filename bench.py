@@ -36,7 +36,7 @@ UNIT = "Mparticles/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 FP32_OPS_PEAK = 152 * 128 * 2.07e9  # FP32 lanes x SMs x max clock (instr/s)
 FP64_OPS_PEAK = 1.25e12 / 2.0       # nominal GB300 FP64 FMA rate (ops/s)
-KERNELS_PER_STEP = 8  # hist, scan, scatter, big, warp(cells), unit(cells), unit(pieces), emit
+KERNELS_PER_STEP = 10  # hist, scan, scatter, big, warp(cells), unit(cells), unit(pieces), count, tiles, emit
 
 
 def load_peaks():

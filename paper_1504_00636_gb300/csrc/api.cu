@@ -78,7 +78,9 @@ struct pma_handle {
   int32_t *warp_list = nullptr, *block_list = nullptr;
   void *fin = nullptr;  // staging: D + 1 columns of capacity entries
   uint8_t *head = nullptr;
-  unsigned long long *bin_status = nullptr, *emit_status = nullptr;
+  unsigned long long *bin_status = nullptr;
+  int32_t *tile_count = nullptr;
+  long long *tile_prefix = nullptr;
   int4 *pieces = nullptr;
   Ctl *ctl = nullptr;
   Ctl *ctl_host = nullptr;
@@ -118,7 +120,7 @@ cudaError_t dalloc(T **p, size_t count) {
 
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
-                  h->big_list, h->head, h->bin_status, h->emit_status,
+                  h->big_list, h->head, h->bin_status, h->tile_count, h->tile_prefix,
                   h->pieces, h->ctl, h->warp_list, h->block_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
@@ -235,7 +237,8 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
             cudaMalloc(&h->fin, (size_t)N * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
-            dalloc(&h->emit_status, h->emit_tiles_max) == cudaSuccess &&
+            dalloc(&h->tile_count, h->emit_tiles_max) == cudaSuccess &&
+            dalloc(&h->tile_prefix, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
             cudaMallocHost(reinterpret_cast<void **>(&h->ctl_host), sizeof(Ctl)) == cudaSuccess;
   if (!ok) {
@@ -290,7 +293,6 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   PMA_CUDA(h, cudaMemsetAsync(h->fill, 0, C * sizeof(int32_t), st));
   PMA_CUDA(h, cudaMemsetAsync(h->bin_status, 0, h->bin_tiles * sizeof(unsigned long long), st));
   const int tiles = emit_tiles_for(n);
-  PMA_CUDA(h, cudaMemsetAsync(h->emit_status, 0, tiles * sizeof(unsigned long long), st));
 
   BinArgs b{};
   b.n = n;
@@ -399,8 +401,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.out_count = out->count_dev;
   m.out_count2 = &h->ctl->count;
   m.err = &h->ctl->err;
-  m.scan_status = h->emit_status;
-  m.scan_ticket = &h->ctl->emit_ticket;
+  m.tile_count = h->tile_count;
+  m.tile_prefix = h->tile_prefix;
   m.tiles = tiles;
   e = launch_emit(m, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "emit launch");

@@ -40,9 +40,14 @@ enum Stat {
 };
 
 // head byte of a final position: 0 inside a final set, 1 first (only)
-// particle of a one-particle set, 2 first particle of a merged set
+// particle of a one-particle set, m (2..254) first particle of a merged set of
+// m particles, 255 first particle of a merged set of 255 or more
 constexpr uint8_t kHeadSingle = 1;
 constexpr uint8_t kHeadMerged = 2;
+constexpr uint8_t kHeadLong = 255;
+__host__ __device__ __forceinline__ uint8_t head_code(int m) {
+  return (uint8_t)(m < 255 ? m : 255);
+}
 
 struct Problem {
   int32_t n_cells;

@@ -59,8 +59,8 @@ struct EmitArgs {
   int64_t *out_count;   // device word(s) receiving M
   int64_t *out_count2;
   unsigned *err;
-  unsigned long long *scan_status;
-  int32_t *scan_ticket;
+  int32_t *tile_count;    // [tiles] heads per tile
+  long long *tile_prefix; // [tiles] heads before each tile
   int32_t tiles;
 };
 int emit_tiles_for(int64_t n);

@@ -71,7 +71,7 @@ template <typename T, int D>
 __device__ void emit_leaf_warp(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
                                int64_t gb, int b, int e, int par, const Moments<T, D> &M,
                                const T *s, int lane) {
-  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
+  const uint8_t h = head_code(e - b);
   for (int j = b + lane; j < e; j += 32) {
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
@@ -84,7 +84,7 @@ template <typename T, int D>
 __device__ void emit_leaf_thread(const Problem &P, const Tile<T, D> &S, const int32_t *perm,
                                  int64_t gb, int b, int e, int par, const Moments<T, D> &M,
                                  const T *s) {
-  const uint8_t h = (e - b == 1) ? kHeadSingle : kHeadMerged;
+  const uint8_t h = head_code(e - b);
   for (int j = b; j < e; ++j) {
     P.perm_final[gb + j] = orig_index(perm, gb, S.id[par][j]);
     P.head[gb + j] = (j == b) ? h : (uint8_t)0;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
       if (cut.leaf) {
         for (int64_t i = b + tid; i < e; i += blockDim.x) {
           P.perm_final[i] = P.perm[i];
-          P.head[i] = (i == b) ? ((e - b == 1) ? kHeadSingle : kHeadMerged) : (uint8_t)0;
+          P.head[i] = (i == b) ? head_code((int)(e - b)) : (uint8_t)0;
           stage_global<T, D>(P, i, P.perm[i]);
         }
         if (tid == 0) {

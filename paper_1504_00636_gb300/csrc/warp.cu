@@ -187,7 +187,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   const int epar = cut.leaf ? par : np;
   // final sets: permutation and head bytes (Step 7 sums them up later)
   if (final_set) {
-    const uint8_t h = (m == 1) ? kHeadSingle : kHeadMerged;
+    const uint8_t h = head_code(m);
     for (int i = gl; i < m; i += G) {
       const int j = S.idx[epar][b + i];
       P.perm_final[gb + b + i] = orig_index(perm, gb, j);
