@@ -66,7 +66,6 @@ struct pma_handle {
   int cap = 0;
   int unit_grid = 0;
   int cap_w = 0;
-  int warps_per_cta = 0;
   int warp_grid = 0;
   int64_t capacity = 0;
   int bin_tiles = 0;
@@ -211,19 +210,19 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
     delete h;
     return PMA_ERR_CUDA;
   }
-  // largest unit that fits one CTA's shared memory (static part ~4 KB)
-  int cap = 8192;
-  while (cap > 64 && unit_smem(h->mixed, h->D, cap) + 4096 > (size_t)smem_optin) cap -= 64;
-  h->cap = cap;
-  h->unit_grid = h->sms;
-  // warp-team class: cells up to cap_w particles, one team of warps each
+  // population classes: cells of up to cap_w particles go to a team of 4
+  // warps (several per SM); cells of up to cap to a team of 8 warps with the
+  // largest tile that fits one CTA; larger cells are cut in global memory
+  // first and their pieces join the large class.
   const size_t smem_sm = (size_t)smem_optin + 1024;
   h->cap_w = 1024;
-  while (h->cap_w > 128 && warp_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
+  while (h->cap_w > 128 && team_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
     h->cap_w -= 64;
-  h->warps_per_cta = 4;
-  const size_t cta_smem = warp_smem(h->mixed, h->D, h->cap_w);
-  h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (cta_smem + 1024)));
+  h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, h->cap_w) + 1024)));
+  int cap = 8191;
+  while (cap > h->cap_w && team_smem(h->mixed, h->D, cap) > (size_t)smem_optin) cap -= 64;
+  h->cap = cap;
+  h->unit_grid = h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, cap) + 1024)));
   const int64_t N = std::max<int64_t>(cfg->capacity, 1);
   const int64_t C = cfg->n_cells;
   h->bin_tiles = scan_tiles_for(C);
@@ -371,14 +370,14 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   e = launch_big(P, h->mixed, h->sms, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);
-  e = launch_warps(P, h->mixed, h->warps_per_cta, h->warp_grid, st);
-  if (e != cudaSuccess) return cuda_fail(h, e, "warp launch (cells)");
+  e = launch_team(P, h->mixed, 0, 4, h->cap_w, h->warp_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "team launch (small cells)");
   mark(h, 3, st);
-  e = launch_units(P, h->mixed, 0, h->unit_grid, st);
-  if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (cells)");
+  e = launch_team(P, h->mixed, 1, 8, h->cap, h->unit_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "team launch (large cells)");
   mark(h, 4, st);
-  e = launch_units(P, h->mixed, 1, h->unit_grid, st);
-  if (e != cudaSuccess) return cuda_fail(h, e, "unit launch (pieces)");
+  e = launch_team(P, h->mixed, 2, 8, h->cap, h->unit_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "team launch (pieces)");
   mark(h, 5, st);
 
   EmitArgs m{};

@@ -10,10 +10,12 @@ namespace pma {
 
 // split.cu
 size_t unit_smem(int mixed, int D, int cap);
-cudaError_t launch_units(const Problem &P, int mixed, int mode, int grid, cudaStream_t st);
 cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st);
-size_t warp_smem(int mixed, int D, int cap_w);
-cudaError_t launch_warps(const Problem &P, int mixed, int warps_per_cta, int grid, cudaStream_t st);
+// warp.cu: a team of `team` (4 or 8) warps per unit of up to `cap` particles;
+// mode 0 small-class cells, 1 large-class cells, 2 pieces of big cells
+size_t team_smem(int mixed, int D, int cap);
+cudaError_t launch_team(const Problem &P, int mixed, int mode, int team, int cap, int grid,
+                        cudaStream_t st);
 
 // bin.cu
 struct BinArgs {

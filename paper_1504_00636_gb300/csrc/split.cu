@@ -1,19 +1,12 @@
-// Recursive Voronoi partition of every cell (Sec. 3, Steps 2-6) and the
-// centroid records of its final sets (Step 7).
+// big_kernel: cells larger than any shared-memory tile are cut (Sec. 3,
+// Steps 2-6) by a whole CTA in global memory, on the permutation array only,
+// until every piece fits; the pieces then go through the team kernel
+// (warp.cu).  Final sets met on the way are emitted here.
 //
-// unit_kernel: one CTA per unit (a whole cell, or a piece of a big cell),
-// particles staged in shared memory as SoA columns, double-buffered by tree
-// depth parity.  A subset is always a contiguous range [b, e) of one buffer;
-// a cut writes V1 = {q_k <= Q_k} to the front and V2 to the back of the same
-// range in the other buffer, so the final sets of a cell end up in V1-first
-// depth-first order when listed by position.
-//   phase A: subsets larger than kSmall are handled one per warp, level by
-//            level (moments by warp reduction, cut by ballot scan);
-//   phase B: subsets of at most kSmall particles are finished by one thread
-//            each, depth-first.
-// big_kernel: cells larger than the shared-memory capacity are cut by a whole
-// CTA in global memory (on the permutation array only) until every piece
-// fits; the pieces then go through unit_kernel.
+// The CTA-per-cell building blocks below (a double-buffered shared-memory
+// tile, warp-level cuts of large subsets, thread-level depth-first finishing
+// of small ones) serve the allocation-free entry point at the end of this
+// file.
 #include <cstddef>
 #include <mutex>
 
@@ -240,129 +233,6 @@ __device__ void thread_finish(const Problem &P, const Tile<T, D> &S, const int32
   }
 }
 
-// ------------------------------------------------------------ unit kernel
-
-// mode 0: units are cells (big cells skipped); mode 1: units are pieces.
-template <typename T, int D>
-__global__ void __launch_bounds__(256) unit_kernel(Problem P, int mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_ctr[4];  // n_cur, n_nxt, n_small, small_next
-  __shared__ int s_unit;
-  __shared__ unsigned long long s_st[kStCount];
-
-  const int cap = P.cap;
-  Tile<T, D> S;
-  S.base = reinterpret_cast<T *>(smem_raw);
-  S.cap = cap;
-  S.id[0] = reinterpret_cast<uint16_t *>(S.base + (size_t)2 * (D + 1) * cap);
-  S.id[1] = S.id[0] + cap;
-  const int max_big = cap / kSmall + 2;
-  Item *lists = reinterpret_cast<Item *>(S.id[1] + cap);
-  Item *cur = lists, *nxt = lists + max_big;
-  Item *small = lists + 2 * max_big;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  if (tid < kStCount) s_st[tid] = 0ull;
-  const int n_units = mode == 0 ? *P.block_count : *P.piece_count;
-  const int32_t *perm = (mode == 0 && *P.unsorted == 0) ? nullptr : P.perm;
-  unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};  // leaves, depth, splits, degenerate
-
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) s_unit = atomicAdd(P.unit_next + mode, 1);
-    __syncthreads();
-    const int u = s_unit;
-    if (u >= n_units) break;
-    int64_t gb;
-    int n, depth0 = 0;
-    if (mode == 0) {
-      const int c = P.block_list[u];
-      gb = P.cell_begin[c];
-      n = P.cell_begin[c + 1] - (int)gb;
-      if (n == 0) continue;
-      if (n <= P.n_min || n == 1) {
-        for (int i = tid; i < n; i += blockDim.x) {
-          const int src = orig_index(perm, gb, i);
-          P.perm_final[gb + i] = src;
-          P.head[gb + i] = kHeadSingle;
-          stage_global<T, D>(P, gb + i, src);
-        }
-        if (tid == 0) s_st[kStCellsPass] += 1;
-        continue;
-      }
-      if (n > cap) continue;  // cut first by big_kernel
-      if (tid == 0) s_st[kStCellsMerged] += 1;
-    } else {
-      int4 pc = P.pieces[u];
-      gb = pc.x;
-      n = pc.y - pc.x;
-      depth0 = pc.z;
-    }
-    // stage the unit in shared memory (validating what is read)
-    bool bad = false;
-    for (int i = tid; i < n; i += blockDim.x) {
-      int src = orig_index(perm, gb, i);
-#pragma unroll
-      for (int l = 0; l < D; ++l) {
-        T x = StoreOf<T>::load(P.q[l], src);
-        bad |= !finite_val(x);
-        S.col(0, l)[i] = x;
-      }
-      T w = StoreOf<T>::load(P.w, src);
-      bad |= !(w > T(0)) || !finite_val(w);
-      S.col(0, D)[i] = w;
-      S.id[0][i] = (uint16_t)i;
-    }
-    if (bad) set_error(P.err, kErrInput);
-    if (tid == 0) {
-      Item root{0, (uint16_t)n, 0, (uint8_t)depth0, 0};
-      s_ctr[0] = 0;
-      s_ctr[1] = 0;
-      s_ctr[2] = 0;
-      s_ctr[3] = 0;
-      if (n <= kSmall) {
-        small[0] = root;
-        s_ctr[2] = 1;
-      } else {
-        cur[0] = root;
-        s_ctr[0] = 1;
-      }
-    }
-    __syncthreads();
-    // phase A: one warp per large subset, level by level
-    for (;;) {
-      const int ncur = s_ctr[0];
-      if (ncur == 0) break;
-      for (int k = warp; k < ncur; k += nwarps)
-        warp_split<T, D>(P, S, perm, gb, cur[k], nxt, &s_ctr[1], max_big, small, &s_ctr[2], s_st,
-                         lane);
-      __syncthreads();
-      if (tid == 0) {
-        s_ctr[0] = min(s_ctr[1], max_big);
-        s_ctr[1] = 0;
-      }
-      Item *t = cur;
-      cur = nxt;
-      nxt = t;
-      __syncthreads();
-    }
-    // phase B: one thread per small subset
-    const int n_small = s_ctr[2];
-    for (;;) {
-      int k = atomicAdd(&s_ctr[3], 1);
-      if (k >= n_small) break;
-      thread_finish<T, D>(P, S, perm, gb, small[k], cnt);
-    }
-  }
-  // flush counters
-  atomicAdd(&s_st[kStLeaves], cnt[0]);
-  atomicAdd(&s_st[kStDepth], cnt[1]);
-  atomicAdd(&s_st[kStSplits], cnt[2]);
-  atomicAdd(&s_st[kStDegenerate], cnt[3]);
-  __syncthreads();
-  if (tid < kStCount && s_st[tid]) atomicAdd(&P.stats[tid], s_st[tid]);
-}
-
 // ------------------------------------------------------------- big kernel
 
 template <typename T, int D>
@@ -523,16 +393,6 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
 // ---------------------------------------------------------------- launch
 
 template <typename T, int D>
-static cudaError_t launch_units_t(const Problem &P, int mode, int grid, cudaStream_t st) {
-  size_t smem = unit_smem_bytes<T, D>(P.cap);
-  cudaError_t e = cudaFuncSetAttribute(unit_kernel<T, D>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  unit_kernel<T, D><<<grid, 256, smem, st>>>(P, mode);
-  return cudaGetLastError();
-}
-
-template <typename T, int D>
 static cudaError_t launch_big_t(const Problem &P, int grid, cudaStream_t st) {
   big_kernel<T, D><<<grid, 512, 0, st>>>(P);
   return cudaGetLastError();
@@ -562,14 +422,6 @@ size_t unit_smem(int mixed, int D, int cap) {
     case 6: return FN<T, 6>(__VA_ARGS__);                 \
     default: return cudaErrorInvalidValue;                \
   }
-
-cudaError_t launch_units(const Problem &P, int mixed, int mode, int grid, cudaStream_t st) {
-  if (mixed) {
-    PMA_DISPATCH_D(launch_units_t, float, P, mode, grid, st)
-  } else {
-    PMA_DISPATCH_D(launch_units_t, double, P, mode, grid, st)
-  }
-}
 
 cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st) {
   if (mixed) {

@@ -25,7 +25,7 @@ namespace pma {
 
 constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
 constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
-constexpr int kMaxCapW = 2047;
+constexpr int kMaxCapW = 8191;
 
 // size class of a subset of m >= 2 particles
 __device__ __forceinline__ int size_class(int m) {
@@ -50,10 +50,13 @@ __host__ __device__ inline int stacks_entries(int cap) {
   return t;
 }
 
-// subset record: begin (11 bits) | length (12 bits) << 11 | parity << 23
+// subset record: begin (13 bits) | length (13 bits) << 13 | parity << 26
 __device__ __forceinline__ uint32_t pack_rec(int b, int m, int par) {
-  return (uint32_t)b | ((uint32_t)m << 11) | ((uint32_t)par << 23);
+  return (uint32_t)b | ((uint32_t)m << 13) | ((uint32_t)par << 26);
 }
+__device__ __forceinline__ int rec_begin(uint32_t r) { return (int)(r & 8191u); }
+__device__ __forceinline__ int rec_len(uint32_t r) { return (int)((r >> 13) & 8191u); }
+__device__ __forceinline__ int rec_par(uint32_t r) { return (int)((r >> 26) & 1u); }
 
 template <typename T, int D>
 struct WarpTile {
@@ -119,7 +122,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   const int gid = lane >> lg, gl = lane & (G - 1);
   const bool act = gid < kw;
   const uint32_t rec = act ? S.stk[c][base - gid] : 0u;
-  const int b = rec & 2047, m = act ? (int)((rec >> 11) & 4095) : 0, par = (rec >> 23) & 1;
+  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
 
   // Steps 1-2: moments about the set's first particle
   T s[D];
@@ -217,7 +220,7 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
   const bool act = lane < kw;
   const uint32_t rec = act ? S.stk[0][base - lane] : 0u;
   if (!act) return;
-  const int b = rec & 2047, par = (rec >> 23) & 1;
+  const int b = rec_begin(rec), par = rec_par(rec);
   const int ja = S.idx[par][b], jb = S.idx[par][b + 1];
   T qa[D], qb[D];
 #pragma unroll
@@ -270,23 +273,41 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
 
 // --------------------------------------------------------------- kernel
 
-constexpr int kTeam = 4;         // warps sharing one cell
-constexpr int kTeamsPerCta = 1;  // CTA of kTeam * kTeamsPerCta warps
+// Work sources: mode 0 the cells of the small class (and pass-through
+// cells), mode 1 the cells of the large class, mode 2 the pieces of cells
+// that were first cut in global memory.
+struct UnitSource {
+  const int32_t *list;
+  const int32_t *count;
+  int32_t *next;
+  int mode;
+};
 
-__device__ __forceinline__ void team_sync(int team) {
-  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(32 * kTeam) : "memory");
+// one unit: first sorted position, size, depth of its root
+__device__ __forceinline__ void unit_at(const Problem &P, const UnitSource &U, int t, int64_t &gb,
+                                        int &n, int &depth0) {
+  if (U.mode == 2) {
+    const int4 pc = P.pieces[t];
+    gb = pc.x;
+    n = pc.y - pc.x;
+    depth0 = pc.z;
+  } else {
+    const int c = U.list[t];
+    gb = P.cell_begin[c];
+    n = P.cell_begin[c + 1] - (int)gb;
+    depth0 = 0;
+  }
 }
 
-template <typename T, int D>
-__global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem P) {
+template <typename T, int D, int TEAM>
+__global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int team = warp / kTeam, wt = warp % kTeam, tt = threadIdx.x % (32 * kTeam);
-  const int cap = P.cap_w;
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, tt = threadIdx.x;
+  constexpr int kThreads = 32 * TEAM;
   WarpTile<T, D> S;
   int *ctl;
   {
-    unsigned char *base = smem_raw + (size_t)team * warp_region_bytes<T, D>(cap);
+    unsigned char *base = smem_raw;
     S.data = reinterpret_cast<T *>(base);
     S.idx[0] = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
     S.idx[1] = S.idx[0] + cap;
@@ -302,25 +323,26 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
     ctl = S.top + kClasses;
     S.cap = cap;
   }
-  const int32_t *perm = (*P.unsorted == 0) ? nullptr : P.perm;
-  const int count = *P.warp_count;
+  const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
+  const int count = *U.count;
+  const int chunk = U.mode == 0 ? kWarpChunk : 1;
   Counters cnt{0ull, 0ull, 0ull, 0ull};
   unsigned long long merged = 0, passed = 0;
 
   for (;;) {
-    if (tt == 0) ctl[0] = atomicAdd(P.warp_next, kWarpChunk);
-    team_sync(team);
+    if (tt == 0) ctl[0] = atomicAdd(U.next, chunk);
+    __syncthreads();
     const int c0 = ctl[0];
-    team_sync(team);
+    __syncthreads();
     if (c0 >= count) break;
-    const int c1 = min(c0 + kWarpChunk, count);
+    const int c1 = min(c0 + chunk, count);
     for (int t = c0; t < c1; ++t) {
-      const int cell = P.warp_list[t];
-      const int64_t gb = P.cell_begin[cell];
-      const int n = P.cell_begin[cell + 1] - (int)gb;
-      if (n <= P.n_min || n == 1) {
+      int64_t gb;
+      int n, depth0;
+      unit_at(P, U, t, gb, n, depth0);
+      if (U.mode != 2 && (n <= P.n_min || n == 1)) {
         // Sec. 3 "Input": cells with at most N_min particles are not merged
-        for (int i = tt; i < n; i += 32 * kTeam) {
+        for (int i = tt; i < n; i += kThreads) {
           const int src = orig_index(perm, gb, i);
           P.perm_final[gb + i] = src;
           P.head[gb + i] = kHeadSingle;
@@ -332,11 +354,18 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
         passed += 1;
         continue;
       }
-      merged += 1;
+      if (n > cap) {
+        if (tt == 0) set_error(P.err, kErrInternal);
+        continue;
+      }
+      if (U.mode != 2) merged += 1;
+      if (tt == 0) cnt.depth += (unsigned long long)depth0 * n;
       if (t + 1 < c1 && !perm && tt < D + 1) {
-        // the next cell of this chunk: pull its columns into L2 meanwhile
-        const int nc = P.warp_list[t + 1];
-        const int64_t nb = P.cell_begin[nc], ne = P.cell_begin[nc + 1];
+        // the next unit of this chunk: pull its columns into L2 meanwhile
+        int64_t nb;
+        int nn, nd;
+        unit_at(P, U, t + 1, nb, nn, nd);
+        const int64_t ne = nb + nn;
         const size_t es = sizeof(T);
         const char *col = static_cast<const char *>(tt < D ? P.q[tt] : P.w);
         // the 16-byte-aligned part of the range only: never outside the array
@@ -349,7 +378,7 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
       }
       bool bad = false;
 #pragma unroll 4
-      for (int i = tt; i < n; i += 32 * kTeam) {
+      for (int i = tt; i < n; i += kThreads) {
         const int src = orig_index(perm, gb, i);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
@@ -364,16 +393,22 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
       if (tt < kClasses) S.top[tt] = 0;
-      team_sync(team);
+      __syncthreads();
       if (tt == 0) {
-        const int c = size_class(n);
-        S.stk[c][0] = pack_rec(0, n, 0);
-        S.top[c] = 1;
+        if (n == 1) {
+          // a one-particle piece is final at once
+          emit_single<T, D>(P, S, perm, gb, 0, 0);
+          cnt.leaves += 1;
+        } else {
+          const int c = size_class(n);
+          S.stk[c][0] = pack_rec(0, n, 0);
+          S.top[c] = 1;
+        }
       }
-      // rounds: the team pops up to kTeam * 32/G subsets of the largest
+      // rounds: the team pops up to TEAM * 32/G subsets of the largest
       // non-empty class; warp wt takes the wt-th share
       for (;;) {
-        team_sync(team);
+        __syncthreads();
         int c = -1;
 #pragma unroll
         for (int k = kClasses - 1; k >= 0; --k)
@@ -381,12 +416,12 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
         if (c < 0) break;
         const int per = (c == 0) ? 32 : (32 >> (c - 1));
         const int avail = S.top[c];
-        const int k = min(avail, kTeam * per);
+        const int k = min(avail, TEAM * per);
         const int kw = max(0, min(per, k - wt * per));
         const int base = avail - 1 - wt * per;
-        team_sync(team);
+        __syncthreads();
         if (tt == 0) S.top[c] = avail - k;
-        team_sync(team);
+        __syncthreads();
         if (kw > 0) {
           if (c == 0)
             pair_round<T, D>(P, S, perm, gb, lane, cnt, kw, base);
@@ -417,7 +452,7 @@ __global__ void __launch_bounds__(32 * kTeam * kTeamsPerCta) warp_kernel(Problem
 // ----------------------------------------------------------------- launch
 
 template <typename T>
-static size_t warp_smem_t(int D, int cap) {
+static size_t team_smem_t(int D, int cap) {
   switch (D) {
     case 2: return warp_region_bytes<T, 2>(cap);
     case 3: return warp_region_bytes<T, 3>(cap);
@@ -427,40 +462,58 @@ static size_t warp_smem_t(int D, int cap) {
   }
 }
 
-// shared memory of one CTA (kTeamsPerCta cells)
-size_t warp_smem(int mixed, int D, int cap_w) {
-  return kTeamsPerCta * (mixed ? warp_smem_t<float>(D, cap_w) : warp_smem_t<double>(D, cap_w));
+// shared memory of one CTA (one team, one unit of up to cap particles)
+size_t team_smem(int mixed, int D, int cap) {
+  return mixed ? team_smem_t<float>(D, cap) : team_smem_t<double>(D, cap);
 }
 
-template <typename T, int D>
-static cudaError_t launch_warps_t(const Problem &P, int grid, cudaStream_t st) {
-  if (P.cap_w > kMaxCapW) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)kTeamsPerCta * warp_region_bytes<T, D>(P.cap_w);
-  cudaError_t e = cudaFuncSetAttribute(warp_kernel<T, D>,
+template <typename T, int D, int TEAM>
+static cudaError_t launch_team_t(const Problem &P, const UnitSource &U, int cap, int grid,
+                                 cudaStream_t st) {
+  if (cap > kMaxCapW) return cudaErrorInvalidValue;
+  const size_t smem = warp_region_bytes<T, D>(cap);
+  cudaError_t e = cudaFuncSetAttribute(team_kernel<T, D, TEAM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  warp_kernel<T, D><<<grid, 32 * kTeam * kTeamsPerCta, smem, st>>>(P);
+  team_kernel<T, D, TEAM><<<grid, 32 * TEAM, smem, st>>>(P, U, cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_warps(const Problem &P, int mixed, int wpc, int grid, cudaStream_t st) {
-  (void)wpc;
-  if (mixed) {
-    switch (P.D) {
-      case 2: return launch_warps_t<float, 2>(P, grid, st);
-      case 3: return launch_warps_t<float, 3>(P, grid, st);
-      case 4: return launch_warps_t<float, 4>(P, grid, st);
-      case 5: return launch_warps_t<float, 5>(P, grid, st);
-      default: return launch_warps_t<float, 6>(P, grid, st);
-    }
-  }
+template <typename T, int TEAM>
+static cudaError_t launch_team_d(const Problem &P, const UnitSource &U, int cap, int grid,
+                                 cudaStream_t st) {
   switch (P.D) {
-    case 2: return launch_warps_t<double, 2>(P, grid, st);
-    case 3: return launch_warps_t<double, 3>(P, grid, st);
-    case 4: return launch_warps_t<double, 4>(P, grid, st);
-    case 5: return launch_warps_t<double, 5>(P, grid, st);
-    default: return launch_warps_t<double, 6>(P, grid, st);
+    case 2: return launch_team_t<T, 2, TEAM>(P, U, cap, grid, st);
+    case 3: return launch_team_t<T, 3, TEAM>(P, U, cap, grid, st);
+    case 4: return launch_team_t<T, 4, TEAM>(P, U, cap, grid, st);
+    case 5: return launch_team_t<T, 5, TEAM>(P, U, cap, grid, st);
+    default: return launch_team_t<T, 6, TEAM>(P, U, cap, grid, st);
   }
+}
+
+// mode: 0 small-class cells, 1 large-class cells, 2 pieces of big cells
+cudaError_t launch_team(const Problem &P, int mixed, int mode, int team, int cap, int grid,
+                        cudaStream_t st) {
+  UnitSource U;
+  U.mode = mode;
+  if (mode == 0) {
+    U.list = P.warp_list;
+    U.count = P.warp_count;
+    U.next = P.warp_next;
+  } else if (mode == 1) {
+    U.list = P.block_list;
+    U.count = P.block_count;
+    U.next = P.unit_next;
+  } else {
+    U.list = nullptr;
+    U.count = P.piece_count;
+    U.next = P.unit_next + 1;
+  }
+  if (team == 4)
+    return mixed ? launch_team_d<float, 4>(P, U, cap, grid, st)
+                 : launch_team_d<double, 4>(P, U, cap, grid, st);
+  return mixed ? launch_team_d<float, 8>(P, U, cap, grid, st)
+               : launch_team_d<double, 8>(P, U, cap, grid, st);
 }
 
 }  // namespace pma
