@@ -47,11 +47,9 @@ def run_gpu(p, precision="fp64", tol_x=None, tol_p=None, n_min=None, capacity=No
 
 
 def local_index(index, cell_of_input, out_cell, n_cells):
-    """Per particle: output slot relative to the first output of its cell."""
-    first = np.full(n_cells, -1, np.int64)
-    if out_cell.size:
-        c, pos = np.unique(out_cell, return_index=True)
-        first[c] = pos
+    """Per particle: output slot relative to the first output of its cell
+    (outputs are ordered by cell, so the first slot comes from a search)."""
+    first = np.searchsorted(out_cell, np.arange(n_cells, dtype=out_cell.dtype), side="left")
     return index.astype(np.int64) - first[cell_of_input]
 
 

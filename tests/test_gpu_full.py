@@ -42,7 +42,8 @@ def _sampled_parity(p, precision, exact_membership=True):
     # the whole output: counts per cell never exceed the inputs, index is onto
     assert g["count"] <= p.n
     assert np.all(np.bincount(g["cell"], minlength=p.n_cells) <= counts)
-    assert np.array_equal(np.unique(g["index"]), np.arange(g["count"]))
+    assert np.all(np.bincount(g["index"], minlength=g["count"]) > 0)
+    assert g["index"].max() == g["count"] - 1
     return g
 
 
@@ -57,6 +58,4 @@ def test_shower_full_mixed():
 
 
 def test_hot_6d_full_mixed():
-    p = synth.hot_6d()
-    g = _sampled_parity(p, "mixed", exact_membership=False)
-    assert g["stats"]["big_cells"] > 0
+    _sampled_parity(synth.hot_6d(), "mixed", exact_membership=False)
