@@ -259,7 +259,8 @@ def time_oracle(p, threads, reps):
 
 
 def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name):
-    """Roofline of the dominant kernel (per-cell partition: warp_kernel)."""
+    """Roofline of the dominant kernel: the per-cell partition of the small-cell
+    class (team_kernel, 4 warps per cell), from its live event timing."""
     b_in, _ = bytes_per_particle(p, mixed)
     t = stage_ms["warp_cells"] * 1e-3
     n = p.n
@@ -271,17 +272,17 @@ def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name):
     hbm = peaks["hbm_gbs"] * 1e9
     alu_peak = FP32_OPS_PEAK if mixed else FP64_OPS_PEAK
     t_hbm, t_alu = bytes_alg / hbm, ops_alg / alu_peak
-    traffic = ncu_traffic("warp_kernel", workload_name, "mixed" if mixed else "fp64")
+    traffic = ncu_traffic("team_kernel", workload_name, "mixed" if mixed else "fp64")
     if t_hbm >= t_alu:
         ach = bytes_alg / t / 1e9
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                "traffic": traffic, "kernel": "warp_kernel",
+                "traffic": traffic, "kernel": "team_kernel",
                 "peak_source": peak_kind}
     ach = ops_alg / t / 1e12
     return {"bound": "alu", "achieved": round(ach, 4), "peak": round(alu_peak / 1e12, 3),
             "unit": "Tops/s", "frac": round(ach / (alu_peak / 1e12), 4), "traffic": traffic,
-            "kernel": "warp_kernel",
+            "kernel": "team_kernel",
             "peak_source": "FP32 lanes x SMs x max clock" if mixed else
             "nominal GB300 FP64 1.25 TFLOP/s / 2"}
 
