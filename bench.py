@@ -194,8 +194,32 @@ def time_device(p, mixed, steps, warmup, dev, flush):
     ms = [a.elapsed_time(b) for a, b in ev]
     st = m.stats()
     M = int(out.count_dev.item())
+    # the same step captured once into a CUDA graph and replayed
+    graph_ms = None
+    try:
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=gs)
+        for _ in range(2):
+            g.replay()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(1.0)
+            gev[k][0].record(stream)
+            g.replay()
+            gev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if int(out.count_dev.item()) == M:
+            graph_ms = [a.elapsed_time(b) for a, b in gev]
+        del g
+    except Exception as exc:  # report, do not fail the eager measurement
+        print("graph capture failed: %r" % (exc,), file=sys.stderr)
     m.close()
-    return dict(ms=ms, stage=stage, stats=st, M=M)
+    return dict(ms=ms, stage=stage, stats=st, M=M, graph_ms=graph_ms)
 
 
 def time_e2e(p, mixed, steps, warmup):
@@ -247,6 +271,68 @@ def time_e2e(p, mixed, steps, warmup):
     return dict(s=ts, h2d=h2d, d2h=d2h, M=M)
 
 
+def accuracy_report(p, dev, sample_cells=256, seed=0):
+    """Mixed path vs the FP64 oracle on sampled cells (outside any timed
+    region): cells whose membership differs, worst coordinate error of the
+    merged particles (relative to each axis' mean |q|), worst per-cell
+    conservation error of W and W P (relative to sum w and sum w |p|).
+    The oracle runs on (a) the float32-rounded inputs the mixed path stores
+    and (b) the original FP64 inputs, separating input rounding from
+    accumulation."""
+    import torch
+    import oracle
+    from paper_1504_00636_gb300 import binding
+    q = p.astype(np.float32)
+    m = binding.Merger(q.dx, q.dp, q.n_cells, q.n, q.cell_size, q.n_min, "mixed")
+    cells, pos, mom, w = to_device(q, True, dev)
+    M, out = m.merge(cells, pos, mom, w, q.tol_x, q.tol_p)
+    g_cell = out.cell[:M].cpu().numpy()
+    g_index = out.index[:q.n].cpu().numpy().astype(np.int64)
+    g_w = out.w[:M].cpu().numpy()
+    g_c = np.concatenate([np.stack([t[:M].cpu().double().numpy() for t in out.pos]),
+                          np.stack([t[:M].cpu().numpy() for t in out.mom])])
+    m.close()
+    rng = np.random.default_rng(seed)
+    present = np.unique(q.cell)
+    sample = np.sort(rng.choice(present, min(sample_cells, present.size), replace=False))
+    first_g = np.searchsorted(g_cell, np.arange(q.n_cells))
+    rep = {"sample_cells": int(sample.size)}
+    for tag, src in (("vs_oracle_on_f32_inputs", q), ("vs_oracle_on_f64_inputs", p)):
+        sub = src.select_cells(sample)
+        r = oracle.merge_particles(sub, threads=os.cpu_count() or 1)
+        mask = np.isin(q.cell, sample)
+        gi = g_index[mask] - first_g[q.cell[mask]]
+        first_o = np.searchsorted(r.cell, np.arange(q.n_cells))
+        oi = r.index.astype(np.int64) - first_o[sub.cell]
+        diff = np.unique(sub.cell[gi != oi])
+        same = np.setdiff1d(sample, diff)
+        go = np.isin(g_cell, same)
+        oo = np.isin(r.cell, same)
+        worst = 0.0
+        if go.sum() == oo.sum() and go.any():
+            ref = np.concatenate([r.pos, r.mom])[:, oo]
+            got = g_c[:, go]
+            scale = np.mean(np.abs(np.concatenate([sub.pos, sub.mom]).astype(np.float64)), axis=1)
+            worst = float(np.max(np.abs(got - ref) / scale[:, None]))
+        rep[tag] = {"cells_differing": int(diff.size), "flagged_near_ties": int((r.flags != 0).sum()),
+                    "max_coord_err_rel": worst}
+    # conservation against the stored (float32) inputs, every sampled cell
+    mask_o = np.isin(g_cell, sample)
+    wq = q.w.astype(np.float64)
+    Win = np.bincount(q.cell, weights=wq, minlength=q.n_cells)[sample]
+    Wout = np.bincount(g_cell[mask_o], weights=g_w[mask_o], minlength=q.n_cells)[sample]
+    worst = float(np.max(np.abs(Wout - Win) / Win))
+    for a in range(q.dp):
+        qa = q.mom[a].astype(np.float64)
+        Sin = np.bincount(q.cell, weights=wq * qa, minlength=q.n_cells)[sample]
+        Ain = np.bincount(q.cell, weights=wq * np.abs(qa), minlength=q.n_cells)[sample]
+        Sout = np.bincount(g_cell[mask_o], weights=g_w[mask_o] * g_c[q.dx + a][mask_o],
+                           minlength=q.n_cells)[sample]
+        worst = max(worst, float(np.max(np.abs(Sout - Sin) / np.maximum(Ain, 1e-300))))
+    rep["conservation_err_rel"] = worst
+    return rep
+
+
 def time_oracle(p, threads, reps):
     import oracle
     oracle.build()
@@ -296,6 +382,7 @@ def main():
     ap.add_argument("--workload", default="two_stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     args = ap.parse_args()
 
@@ -376,7 +463,9 @@ def main():
             M=res["M"], stage_ms={k: round(x, 4) for k, x in res["stage"].items()},
             roofline=roofline(q, mixed, res["stats"], res["stage"], peaks, peak_kind,
                               res["M"], args.workload),
-            depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"])
+            depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"],
+            graph_ms_per_step=(round(float(np.mean(res["graph_ms"])), 4)
+                               if res["graph_ms"] else None))
     if rank != 0:
         return
     head = lines[True] if True in lines else lines[False]
@@ -387,11 +476,13 @@ def main():
             "dtype": "f32/f64" if mixed_head else "f64", "data": "synthetic", "config": cfg,
             "roofline": head["roofline"], "hbm_frac_step": head["hbm_frac_step"],
             "stage_ms": head["stage_ms"], "M": head["M"],
+            "graph_ms_per_step": head["graph_ms_per_step"],
             "gpu_launches": KERNELS_PER_STEP * args.steps * len(lines),
             "clocks": clk}
     if mixed_head and False in lines:
         f = lines[False]
         line["fp64_plain"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
+                              "graph_ms_per_step": f["graph_ms_per_step"],
                               "roofline": f["roofline"], "stage_ms": f["stage_ms"], "M": f["M"],
                               "speedup_mixed_over_fp64": round(head["value"] / f["value"], 3)}
     if not args.no_e2e:
@@ -400,6 +491,8 @@ def main():
         ev = p.n / float(np.mean(e["s"])) / 1e6
         line["e2e"] = {"value": round(ev, 2), "unit": UNIT, "h2d_bytes_per_step": e["h2d"],
                        "d2h_bytes_per_step": e["d2h"]}
+    if mixed_head and not args.no_accuracy:
+        line["accuracy_mixed"] = accuracy_report(p, dev)
     if not args.no_cpu:
         threads = os.cpu_count() or 1
         ts, _ = time_oracle(p, threads, 3)

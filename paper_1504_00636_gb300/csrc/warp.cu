@@ -472,9 +472,18 @@ static cudaError_t launch_team_t(const Problem &P, const UnitSource &U, int cap,
                                  cudaStream_t st) {
   if (cap > kMaxCapW) return cudaErrorInvalidValue;
   const size_t smem = warp_region_bytes<T, D>(cap);
-  cudaError_t e = cudaFuncSetAttribute(team_kernel<T, D, TEAM>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // raise the dynamic shared-memory limit once per device (so that calls
+  // captured into a graph after a first eager call make no attribute change)
+  static int limit_set[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
+    e = cudaFuncSetAttribute(team_kernel<T, D, TEAM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
+  }
   team_kernel<T, D, TEAM><<<grid, 32 * TEAM, smem, st>>>(P, U, cap);
   return cudaGetLastError();
 }

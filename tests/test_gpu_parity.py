@@ -235,3 +235,35 @@ def test_mixed_verbatim_copies_are_exact_for_special_values():
     np.testing.assert_array_equal(g["mom"], p.mom.astype(np.float64))
     assert np.array_equal(np.signbit(g["mom"]), np.signbit(p.mom))
     np.testing.assert_array_equal(g["w"], p.w.astype(np.float64))
+
+
+def test_merge_step_replays_from_a_cuda_graph():
+    # the whole call (binning, partition, emit, status copy) is stream-ordered
+    # with no host synchronisation, so it can be captured once and replayed
+    import torch
+    p = synth.two_stream(cells=64).astype(np.float32)
+    m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, "mixed")
+    dev = torch.device("cuda", 0)
+    cells = torch.from_numpy(p.cell).to(dev)
+    pos = [torch.from_numpy(p.pos[0].copy()).to(dev)]
+    mom = [torch.from_numpy(p.mom[a].copy()).to(dev) for a in range(3)]
+    w = torch.from_numpy(p.w).to(dev)
+    ref_M, ref = m.merge(cells, pos, mom, w, p.tol_x, p.tol_p)
+    out = m.alloc_output(dev)
+    s = torch.cuda.Stream(dev)
+    with torch.cuda.stream(s):
+        m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=s)  # warm-up
+    s.synchronize()
+    m.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=s)
+    for _ in range(3):
+        out.index.fill_(-1)
+        out.count_dev.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(out.count_dev.item()) == ref_M
+        assert torch.equal(out.index, ref.index)
+        assert torch.equal(out.w[:ref_M], ref.w[:ref_M])
+    m.close()
