@@ -8,10 +8,12 @@ The headline `value` is the mixed-precision path (float32 storage,
 compensated float32 moments, FP64-certain decisions, FP64 merged W and P);
 the plain FP64 path on the same particles is reported beside it.
 
-Timing: inputs resident on the device; W untimed warm-up steps; K timed steps
-enqueued back to back, each bracketed by CUDA events on the library's stream,
-with a 256 MB L2 flush between steps (outside the events).  Under torchrun
-(N > 1) every rank runs its own replica; the time is the max over ranks.
+Timing: inputs resident on the device; W untimed warm-up steps; the step is
+captured once into a CUDA graph, and K replays are timed, each bracketed by
+CUDA events on the capture stream, with a 256 MB L2 flush before each step
+(outside the events).  Per-kernel durations come from the library's event
+nodes inside the graph.  Under torchrun (N > 1) every rank runs its own
+replica; the time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -167,59 +169,67 @@ def to_device(p, mixed, dev):
 
 
 def time_device(p, mixed, steps, warmup, dev, flush):
+    """K steps of one pma_merge each, inputs resident.  The step is captured
+    once into a CUDA graph and replayed; each replay is bracketed by CUDA
+    events on the capture stream, and the library's per-stage event nodes
+    (recorded inside the graph) give the kernel durations of every replay.
+    If capture fails, the same loop runs eagerly.  An eager loop is timed
+    beside it for reference."""
     import torch
     from paper_1504_00636_gb300 import binding
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min,
                        "mixed" if mixed else "fp64")
     cells, pos, mom, w = to_device(p, mixed, dev)
     out = m.alloc_output(dev)
-    stream = torch.cuda.current_stream(dev)
-    for _ in range(warmup):
-        flush.fill_(1.0)
-        m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=stream)
-    m.sync()
-    m.set_timing(True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
-    torch.cuda.synchronize(dev)
-    for k in range(steps):
-        flush.fill_(1.0)
-        ev[k][0].record(stream)
-        m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize(dev)
-    m.sync()
-    stage = m.timing()
-    m.set_timing(False)
-    ms = [a.elapsed_time(b) for a, b in ev]
-    st = m.stats()
-    M = int(out.count_dev.item())
-    # the same step captured once into a CUDA graph and replayed
-    graph_ms = None
-    try:
-        gs = torch.cuda.Stream(dev)
-        gs.wait_stream(stream)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=gs):
-            m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=gs)
-        for _ in range(2):
-            g.replay()
-        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        torch.cuda.synchronize(dev)
-        for k in range(steps):
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
             flush.fill_(1.0)
-            gev[k][0].record(stream)
-            g.replay()
-            gev[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-        if int(out.count_dev.item()) == M:
-            graph_ms = [a.elapsed_time(b) for a, b in gev]
-        del g
-    except Exception as exc:  # report, do not fail the eager measurement
+            m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=stream)
+    stream.synchronize()
+    m.sync()
+    M = int(out.count_dev.item())
+
+    def run(step):
+        ms, stages = [], []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+            stream.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stages.append(m.timing())
+        return ms, {k: float(np.mean([s_[k] for s_ in stages])) for k in stages[0]}
+
+    def eager():
+        m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=stream)
+
+    m.set_timing(True)
+    graph_ok = False
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            eager()
+        g.replay()
+        stream.synchronize()
+        graph_ok = int(out.count_dev.item()) == M
+    except Exception as exc:  # fall back to eager launches
         print("graph capture failed: %r" % (exc,), file=sys.stderr)
+    if graph_ok:
+        ms, stage = run(g.replay)
+    else:
+        ms, stage = run(eager)
+    m.set_timing(True)  # fresh ring for the eager comparison
+    eager_ms, _ = run(eager)
+    m.set_timing(False)
+    m.sync()
+    st = m.stats()
     m.close()
-    return dict(ms=ms, stage=stage, stats=st, M=M, graph_ms=graph_ms)
+    return dict(ms=ms, stage=stage, stats=st, M=M, graph=graph_ok, eager_ms=eager_ms)
 
 
 def time_e2e(p, mixed, steps, warmup):
@@ -464,8 +474,8 @@ def main():
             roofline=roofline(q, mixed, res["stats"], res["stage"], peaks, peak_kind,
                               res["M"], args.workload),
             depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"],
-            graph_ms_per_step=(round(float(np.mean(res["graph_ms"])), 4)
-                               if res["graph_ms"] else None))
+            graph=res["graph"],
+            eager_ms_per_step=round(float(np.mean(res["eager_ms"])), 4))
     if rank != 0:
         return
     head = lines[True] if True in lines else lines[False]
@@ -476,13 +486,13 @@ def main():
             "dtype": "f32/f64" if mixed_head else "f64", "data": "synthetic", "config": cfg,
             "roofline": head["roofline"], "hbm_frac_step": head["hbm_frac_step"],
             "stage_ms": head["stage_ms"], "M": head["M"],
-            "graph_ms_per_step": head["graph_ms_per_step"],
+            "cuda_graph": head["graph"], "eager_ms_per_step": head["eager_ms_per_step"],
             "gpu_launches": KERNELS_PER_STEP * args.steps * len(lines),
             "clocks": clk}
     if mixed_head and False in lines:
         f = lines[False]
         line["fp64_plain"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
-                              "graph_ms_per_step": f["graph_ms_per_step"],
+                              "cuda_graph": f["graph"], "eager_ms_per_step": f["eager_ms_per_step"],
                               "roofline": f["roofline"], "stage_ms": f["stage_ms"], "M": f["M"],
                               "speedup_mixed_over_fp64": round(head["value"] / f["value"], 3)}
     if not args.no_e2e:
