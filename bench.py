@@ -11,8 +11,8 @@ the plain FP64 path on the same particles is reported beside it.
 Timing: inputs resident on the device; W untimed warm-up steps; the step is
 captured once into a CUDA graph, and K replays are timed, each bracketed by
 CUDA events on the capture stream, with a 256 MB L2 flush before each step
-(outside the events).  Per-kernel durations come from the library's event
-nodes inside the graph.  Under torchrun (N > 1) every rank runs its own
+(outside the events).  Per-kernel durations come from K eager steps timed
+right after with the library's per-stage events on the same stream.  Under torchrun (N > 1) every rank runs its own
 replica; the time is the max over ranks.
 """
 from __future__ import annotations
@@ -171,10 +171,9 @@ def to_device(p, mixed, dev):
 def time_device(p, mixed, steps, warmup, dev, flush):
     """K steps of one pma_merge each, inputs resident.  The step is captured
     once into a CUDA graph and replayed; each replay is bracketed by CUDA
-    events on the capture stream, and the library's per-stage event nodes
-    (recorded inside the graph) give the kernel durations of every replay.
-    If capture fails, the same loop runs eagerly.  An eager loop is timed
-    beside it for reference."""
+    events on the capture stream (if capture fails, the same loop runs
+    eagerly).  Then K eager steps on the same stream are timed with the
+    library's per-stage events, which give the kernel durations."""
     import torch
     from paper_1504_00636_gb300 import binding
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min,
@@ -191,24 +190,24 @@ def time_device(p, mixed, steps, warmup, dev, flush):
     m.sync()
     M = int(out.count_dev.item())
 
-    def run(step):
-        ms, stages = [], []
-        for _ in range(steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
+    def run(step, stages=False):
+        ms = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stream.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
                 flush.fill_(1.0)
-                e0.record(stream)
+                ev[k][0].record(stream)
                 step()
-                e1.record(stream)
-            stream.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            stages.append(m.timing())
-        return ms, {k: float(np.mean([s_[k] for s_ in stages])) for k in stages[0]}
+                ev[k][1].record(stream)
+        stream.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, (m.timing() if stages else None)
 
     def eager():
         m.merge(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, sync=False, stream=stream)
 
-    m.set_timing(True)
     graph_ok = False
     try:
         g = torch.cuda.CUDAGraph()
@@ -219,12 +218,11 @@ def time_device(p, mixed, steps, warmup, dev, flush):
         graph_ok = int(out.count_dev.item()) == M
     except Exception as exc:  # fall back to eager launches
         print("graph capture failed: %r" % (exc,), file=sys.stderr)
-    if graph_ok:
-        ms, stage = run(g.replay)
-    else:
-        ms, stage = run(eager)
-    m.set_timing(True)  # fresh ring for the eager comparison
-    eager_ms, _ = run(eager)
+    ms, _ = run(g.replay if graph_ok else eager)
+    # per-kernel durations: the library's stage events around the same
+    # kernels, launched eagerly on the same stream right after
+    m.set_timing(True)
+    eager_ms, stage = run(eager, stages=True)
     m.set_timing(False)
     m.sync()
     st = m.stats()
