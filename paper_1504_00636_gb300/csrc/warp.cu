@@ -26,8 +26,6 @@ namespace pma {
 constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
 constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
 constexpr int kMaxCapW = 8191;
-constexpr int kMaxTeam = 8;
-constexpr size_t kWideScratch = kMaxTeam * (sizeof(double) * (2 * kMaxD + 1) + 2 * sizeof(int));
 
 // size class of a subset of m >= 2 particles
 __device__ __forceinline__ int size_class(int m) {
@@ -66,7 +64,6 @@ struct WarpTile {
   uint16_t *idx[2];  // index arrays, by depth parity
   uint32_t *stk[kClasses];
   int *top;          // [kClasses]
-  unsigned char *xch; // cross-warp exchange area of wide rounds
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
 };
@@ -76,8 +73,6 @@ __host__ __device__ inline size_t warp_region_bytes(int cap) {
   size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
   b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 4) * sizeof(int);
-  b = (b + 15) & ~size_t(15);
-  b += kWideScratch;  // cross-warp exchange of wide rounds
   return (b + 15) & ~size_t(15);
 }
 
@@ -276,112 +271,6 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
   }
 }
 
-// ----------------------------------------- wide rounds (several warps)
-
-// Largest class with fewer pending subsets than warps: each subset gets W
-// warps (G = 32 W lanes).  Every thread of the CTA calls this (it contains
-// CTA barriers).  Moments: lane-strided sums, a warp butterfly, then the W
-// warp partials combined in warp order through shared memory.  Cut: each lane
-// owns a contiguous block of the range; a team-wide scan of the block counts
-// places V1 at the front and V2 (reversed) at the back of the other buffer.
-template <typename T, int D, int TEAM>
-__device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                           int64_t gb, int c, int avail, int W, Counters &cnt) {
-  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5;
-  const int sub = wt / W, wl = wt % W, G = 32 * W, gl = wl * 32 + lane;
-  const bool act = sub < avail;
-  const uint32_t rec = act ? S.stk[c][avail - 1 - sub] : 0u;
-  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
-  Moments<T, D> *xm = reinterpret_cast<Moments<T, D> *>(S.xch);
-  int *xs = reinterpret_cast<int *>(S.xch + kMaxTeam * sizeof(Moments<T, D>));
-  T s[D];
-  {
-    const int j0 = act ? S.idx[par][b] : 0;
-#pragma unroll
-    for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
-  }
-  Moments<T, D> M;
-  M.zero();
-#pragma unroll 4
-  for (int i = gl; i < m; i += G) {
-    const int j = S.idx[par][b + i];
-    T q[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
-    M.add(S.col(D)[j], q, s);
-  }
-  M.warp_allreduce();
-  if (lane == 0) xm[wt] = M;
-  __syncthreads();
-  M = xm[sub * W];
-  for (int k = 1; k < W; ++k) M.merge(xm[sub * W + k]);
-  Cut cut;
-  cut.leaf = 1;
-  cut.k = 0;
-  cut.Q = 0.0;
-  cut.Qt = 0.f;
-  if (act) cut = Decider<T, D>::run(P, M, s);
-  const bool split = act && !cut.leaf;
-  // pass 1: V1 count of my contiguous block
-  const int per = (m + G - 1) / G;
-  const int i0 = min(m, gl * per), i1 = min(m, i0 + per);
-  const T *qk = S.col(cut.k);
-  int cl = 0;
-  if (split)
-    for (int i = i0; i < i1; ++i) cl += Decider<T, D>::left(qk[S.idx[par][b + i]], cut) ? 1 : 0;
-  // exclusive scan of cl over the group's lanes (warp scan, then warps)
-  int x = cl;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, d);
-    if (lane >= d) x += y;
-  }
-  if (lane == 31) xs[wt] = x;
-  __syncthreads();
-  int before = 0, total = 0;
-  for (int k = 0; k < W; ++k) {
-    const int v = xs[sub * W + k];
-    if (k < wl) before += v;
-    total += v;
-  }
-  const int prefL = before + x - cl;   // V1 particles before my block
-  const int prefR = i0 - prefL;        // V2 particles before my block
-  const int np = par ^ 1;
-  if (split) {
-    int nl = 0, nr = 0;
-    for (int i = i0; i < i1; ++i) {
-      const int j = S.idx[par][b + i];
-      const int dst = Decider<T, D>::left(qk[j], cut) ? (b + prefL + nl++) : (b + m - 1 - prefR - nr++);
-      S.idx[np][dst] = (uint16_t)j;
-    }
-  }
-  __syncthreads();
-  const int cntL = total;
-  const bool degenerate = split && (cntL == 0 || cntL == m);
-  const bool final_set = act && (cut.leaf || degenerate);
-  const int epar = cut.leaf ? par : np;
-  if (final_set) {
-    const uint8_t h = head_code(m);
-    for (int i = gl; i < m; i += G) {
-      const int j = S.idx[epar][b + i];
-      P.perm_final[gb + b + i] = orig_index(perm, gb, j);
-      P.head[gb + b + i] = (i == 0) ? h : (uint8_t)0;
-      stage<T, D>(P, S, gb + b + i, j);
-    }
-  }
-  if (gl == 0 && act) {
-    if (final_set) {
-      cnt.leaves += 1;
-      if (degenerate) cnt.degenerate += 1;
-    } else {
-      cnt.splits += 1;
-      cnt.depth += (unsigned long long)m;
-      push_child<T, D>(P, S, perm, gb, b, cntL, np, cnt);
-      push_child<T, D>(P, S, perm, gb, b + cntL, m - cntL, np, cnt);
-    }
-  }
-}
-
 // --------------------------------------------------------------- kernel
 
 // Work sources: mode 0 the cells of the small class (and pass-through
@@ -432,8 +321,6 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
     }
     S.top = reinterpret_cast<int *>(st);
     ctl = S.top + kClasses;
-    S.xch = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(ctl + 4) + 15) & ~uintptr_t(15));
     S.cap = cap;
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
@@ -529,16 +416,6 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
         if (c < 0) break;
         const int per = (c == 0) ? 32 : (32 >> (c - 1));
         const int avail = S.top[c];
-        if (c == kClasses - 1 && avail * 2 <= TEAM) {
-          // fewer large subsets than warps: W = TEAM / 2^ceil(log2 avail) warps each
-          int W = TEAM;
-          while (W * avail > TEAM) W >>= 1;
-          __syncthreads();
-          if (tt == 0) S.top[c] = 0;
-          __syncthreads();
-          wide_round<T, D, TEAM>(P, S, perm, gb, c, avail, W, cnt);
-          continue;
-        }
         const int k = min(avail, TEAM * per);
         const int kw = max(0, min(per, k - wt * per));
         const int base = avail - 1 - wt * per;
