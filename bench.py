@@ -38,7 +38,14 @@ UNIT = "Mparticles/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 FP32_OPS_PEAK = 152 * 128 * 2.07e9  # FP32 lanes x SMs x max clock (instr/s)
 FP64_OPS_PEAK = 1.25e12 / 2.0       # nominal GB300 FP64 FMA rate (ops/s)
-KERNELS_PER_STEP = 10  # hist, scan, scatter, big, warp(cells), unit(cells), unit(pieces), count, tiles, emit
+
+
+def kernels_per_step(n_cells):
+    """Library kernels one merge call launches: hist, scan, radix prep, one
+    radix pass per 8-bit digit of the cell id (these return at once on
+    grouped input), big-cell cuts, three team launches, count, tiles, emit."""
+    bits = max(1, int(n_cells).bit_length())
+    return 2 + 1 + (bits + 7) // 8 + 1 + 3 + 3
 
 
 def load_peaks():
@@ -57,6 +64,8 @@ def workload(name):
         return synth.two_stream()
     if name == "two_stream_small":
         return synth.two_stream(cells=1024)
+    if name == "two_stream_shuffled":
+        return synth.two_stream().shuffled(3)
     if name == "shower":
         return synth.shower()
     if name == "hot_6d":
@@ -485,7 +494,7 @@ def main():
             "roofline": head["roofline"], "hbm_frac_step": head["hbm_frac_step"],
             "stage_ms": head["stage_ms"], "M": head["M"],
             "cuda_graph": head["graph"], "eager_ms_per_step": head["eager_ms_per_step"],
-            "gpu_launches": KERNELS_PER_STEP * args.steps * len(lines),
+            "gpu_launches": kernels_per_step(p.n_cells) * args.steps * len(lines),
             "clocks": clk}
     if mixed_head and False in lines:
         f = lines[False]

@@ -3,7 +3,8 @@
 //
 // One call of pma_merge enqueues, on the caller's stream and without any host
 // synchronisation:
-//   hist / scan / scatter   Step 1: cells -> sorted positions
+//   hist / scan             Step 1: per-cell counts and first positions
+//   radix prep / passes     Step 1 for ungrouped input: stable sort by cell
 //   big_kernel              cells too large for shared memory: top cuts in
 //                           global memory until every piece fits
 //   unit_kernel (cells)     Steps 2-6 per cell in shared memory
@@ -36,6 +37,7 @@ struct Ctl {
   int32_t block_count;
   int32_t bin_ticket;
   int32_t emit_ticket;
+  int32_t radix_ticket[kRadixMaxPasses];
   int32_t pad;
   int64_t count;
   unsigned long long stats[kStCount];
@@ -72,7 +74,8 @@ struct pma_handle {
   int emit_tiles_max = 0;
   int max_pieces = 0;
   // workspace
-  int32_t *counts = nullptr, *cell_begin = nullptr, *fill = nullptr;
+  int32_t *counts = nullptr, *cell_begin = nullptr, *radix_count = nullptr;
+  unsigned long long *radix_status = nullptr;
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
   int32_t *warp_list = nullptr, *block_list = nullptr;
   void *fin = nullptr;  // staging: D + 1 columns of capacity entries
@@ -118,7 +121,7 @@ cudaError_t dalloc(T **p, size_t count) {
 }
 
 void free_all(pma_handle *h) {
-  void *ptrs[] = {h->counts, h->cell_begin, h->fill, h->perm, h->perm_tmp, h->perm_final,
+  void *ptrs[] = {h->counts, h->cell_begin, h->radix_count, h->radix_status, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->bin_status, h->tile_count, h->tile_prefix,
                   h->pieces, h->ctl, h->warp_list, h->block_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
@@ -230,7 +233,9 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   h->max_pieces = (int)std::min<int64_t>(N, N / 64 + 4096);
   const int64_t Npad = (N + 15) / 16 * 16;
   bool ok = dalloc(&h->counts, C) == cudaSuccess && dalloc(&h->cell_begin, C + 1) == cudaSuccess &&
-            dalloc(&h->fill, C) == cudaSuccess && dalloc(&h->perm, N) == cudaSuccess &&
+            dalloc(&h->radix_count, kRadixMaxPasses * kRadixBins) == cudaSuccess &&
+            dalloc(&h->radix_status, (size_t)2 * radix_tiles_for(N) * kRadixBins) == cudaSuccess &&
+            dalloc(&h->perm, N) == cudaSuccess &&
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
@@ -289,7 +294,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
     return PMA_OK;
   }
   PMA_CUDA(h, cudaMemsetAsync(h->counts, 0, C * sizeof(int32_t), st));
-  PMA_CUDA(h, cudaMemsetAsync(h->fill, 0, C * sizeof(int32_t), st));
+  PMA_CUDA(h, cudaMemsetAsync(h->radix_count, 0, kRadixMaxPasses * kRadixBins * sizeof(int32_t), st));
   PMA_CUDA(h, cudaMemsetAsync(h->bin_status, 0, h->bin_tiles * sizeof(unsigned long long), st));
   const int tiles = emit_tiles_for(n);
 
@@ -301,7 +306,6 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   b.n_min = h->cfg.n_min;
   b.counts = h->counts;
   b.cell_begin = h->cell_begin;
-  b.fill = h->fill;
   b.perm = h->perm;
   b.unsorted = &h->ctl->unsorted;
   b.big_list = h->big_list;
@@ -315,6 +319,20 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   b.scan_status = h->bin_status;
   b.scan_ticket = &h->ctl->bin_ticket;
   b.scan_tiles = h->bin_tiles;
+  radix_plan(b);
+  b.radix_tiles = radix_tiles_for(n);
+  b.radix_count = h->radix_count;
+  b.radix_ticket = h->ctl->radix_ticket;
+  b.radix_status = h->radix_status;
+  {
+    // intermediate keys in the first two staging columns (written only after
+    // Step 1), intermediate indices in the two spare permutation arrays
+    const size_t es = h->mixed ? 4 : 8;
+    b.radix_keys[0] = reinterpret_cast<int32_t *>(h->fin);
+    b.radix_keys[1] = reinterpret_cast<int32_t *>(static_cast<char *>(h->fin) + (size_t)h->capacity * es);
+    b.radix_vals[0] = h->perm_tmp;
+    b.radix_vals[1] = h->perm_final;
+  }
   h->cur_ev = h->timing ? h->ev[h->timed % kRing] : nullptr;
   mark(h, 0, st);
   cudaError_t e = launch_binning(b, h->sms, st);

@@ -6,8 +6,12 @@
 // scan_kernel   exclusive prefix of the counts -> first sorted position of
 //               every cell (single pass, decoupled look-back), and the list of
 //               cells too large for one CTA's shared memory.
-// scatter_kernel  (only for ungrouped input) writes the permutation
-//               sorted position -> input index.
+// radix_prep_kernel, radix_pass_kernel
+//               (only for ungrouped input) a stable least-significant-digit
+//               radix sort of the cell ids, one pass per digit of up to 8
+//               bits, gives the permutation sorted position -> input index
+//               in (cell, input index) order, so the result does not depend
+//               on how the GPU schedules the work.
 #include "lookback.cuh"
 #include "pma_launch.h"
 
@@ -84,26 +88,137 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
   }
 }
 
-__global__ void scatter_kernel(BinArgs a) {
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixWarps = kRadixThreads / 32;
+static_assert(kRadixThreads == kRadixBins, "one thread per digit");
+
+int radix_tiles_for(int64_t n) { return (int)((n + kRadixTile - 1) / kRadixTile); }
+
+void radix_plan(BinArgs &a) {
+  // keys 0..n_cells (n_cells = invalid id), so bits for the value n_cells
+  int bits = 1;
+  while (bits < 32 && ((int64_t)1 << bits) <= (int64_t)a.n_cells) ++bits;
+  const int passes = (bits + 7) / 8;
+  const int per = (bits + passes - 1) / passes;
+  a.radix_passes = passes;
+  for (int p = 0; p < kRadixMaxPasses; ++p) {
+    a.radix_shift[p] = p * per;
+    a.radix_bits[p] = p < passes ? std::min(per, bits - p * per) : 0;
+  }
+}
+
+__device__ __forceinline__ unsigned radix_key(const BinArgs &a, int c) {
+  return (c < 0 || c >= a.n_cells) ? (unsigned)a.n_cells : (unsigned)c;
+}
+
+// digit counts of every pass, and the first pass's look-back words cleared
+__global__ void __launch_bounds__(kRadixThreads) radix_prep_kernel(BinArgs a) {
   if (*a.unsorted == 0) return;
-  const int lane = threadIdx.x & 31;
+  __shared__ int s_count[kRadixMaxPasses][kRadixBins];
+  for (int k = threadIdx.x; k < kRadixMaxPasses * kRadixBins; k += blockDim.x)
+    (&s_count[0][0])[k] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const unsigned key = radix_key(a, a.cells[i]);
+    for (int p = 0; p < a.radix_passes; ++p)
+      atomicAdd(&s_count[p][(key >> a.radix_shift[p]) & ((1u << a.radix_bits[p]) - 1u)], 1);
+  }
+  const int64_t words = (int64_t)a.radix_tiles * kRadixBins;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < words; k += stride)
+    a.radix_status[k] = 0ull;
+  __syncthreads();
+  for (int p = 0; p < a.radix_passes; ++p) {
+    const int v = s_count[p][threadIdx.x];
+    if (v) atomicAdd(&a.radix_count[p * kRadixBins + threadIdx.x], v);
+  }
+}
+
+// One stable counting pass over key bits [shift, shift + bits).  Every warp
+// ranks a contiguous run of 32 * kRadixItems keys in input order (match on
+// the digit, running per-warp counts), the CTA combines its warps, and each
+// digit's offset across tiles comes from a per-digit decoupled look-back.
+__global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, int p) {
+  if (*a.unsorted == 0) return;
+  __shared__ int s_tile;
+  __shared__ int s_hist[kRadixWarps][kRadixBins];
+  __shared__ int s_base[kRadixBins];
+  __shared__ int s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = tid; k < kRadixWarps * kRadixBins; k += kRadixThreads) (&s_hist[0][0])[k] = 0;
+  if (tid == 0) s_tile = atomicAdd(&a.radix_ticket[p], 1);
+  // first sorted position of every digit of this pass
+  int total;
+  const int digit_base = block_exclusive_scan(a.radix_count[p * kRadixBins + tid], s_warp, &total);
+  const int tile = s_tile;  // published by the scan's barriers
+  const size_t region = (size_t)a.radix_tiles * kRadixBins;
+  unsigned long long *status = a.radix_status + (size_t)(p & 1) * region;
+  // the next pass uses the other region: clear this tile's words of it
+  if (p + 1 < a.radix_passes) a.radix_status[(size_t)((p + 1) & 1) * region +
+                                             (size_t)tile * kRadixBins + tid] = 0ull;
+  const bool first = p == 0, last = p + 1 == a.radix_passes;
+  const int32_t *keys_in = first ? nullptr : a.radix_keys[(p - 1) & 1];
+  const int32_t *vals_in = first ? nullptr : a.radix_vals[(p - 1) & 1];
+  const unsigned shift = a.radix_shift[p], mask = (1u << a.radix_bits[p]) - 1u;
+  const int64_t seg = (int64_t)tile * kRadixTile + (int64_t)warp * (32 * kRadixItems);
+  unsigned key[kRadixItems];
+  int val[kRadixItems], rank[kRadixItems];
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const int64_t i = seg + j * 32 + lane;
+    key[j] = 0xffffffffu;  // beyond n
+    val[j] = -1;
+    if (i < a.n) {
+      if (first) {
+        key[j] = radix_key(a, a.cells[i]);
+        val[j] = (int)i;
+      } else {
+        key[j] = (unsigned)keys_in[i];
+        val[j] = vals_in[i];
+      }
+    }
+  }
   unsigned lt;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n;
-       base += stride) {
-    int64_t i = base + lane;
-    int c = -1;
-    if (i < a.n) {
-      c = a.cells[i];
-      if (c < 0 || c >= a.n_cells) c = -1;
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    const int d = key[j] == 0xffffffffu ? kRadixBins : (int)((key[j] >> shift) & mask);
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int before = d < kRadixBins ? s_hist[warp][d] : 0;
+    __syncwarp();
+    if (d < kRadixBins && lane == __ffs(peers) - 1) s_hist[warp][d] = before + __popc(peers);
+    __syncwarp();
+    rank[j] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  // digit tid: offsets of the warps inside the tile, then across tiles
+  int run = 0;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) {
+    const int t = s_hist[w][tid];
+    s_hist[w][tid] = run;
+    run += t;
+  }
+  const long long before_tile = tile_exclusive_prefix(status + tid, tile, run, a.err, kRadixBins);
+  s_base[tid] = digit_base + (int)before_tile;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kRadixItems; ++j) {
+    if (key[j] == 0xffffffffu) continue;
+    const int d = (int)((key[j] >> shift) & mask);
+    const int64_t pos = (int64_t)s_base[d] + s_hist[warp][d] + rank[j];
+    if ((uint64_t)pos >= (uint64_t)a.n) {  // only after a failed look-back
+      atomicOr(a.err, kErrInternal);
+      continue;
     }
-    unsigned grp = __match_any_sync(0xffffffffu, c);
-    int leader = __ffs(grp) - 1;
-    int off = 0;
-    if (c >= 0 && lane == leader) off = atomicAdd(&a.fill[c], __popc(grp));
-    off = __shfl_sync(0xffffffffu, off, leader);
-    if (c >= 0) a.perm[a.cell_begin[c] + off + __popc(grp & lt)] = (int32_t)i;
+    if (last) {
+      a.perm[pos] = val[j];
+    } else {
+      a.radix_keys[p & 1][pos] = (int32_t)key[j];
+      a.radix_vals[p & 1][pos] = val[j];
+    }
   }
 }
 
@@ -114,8 +229,11 @@ cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st) {
   }
   scan_kernel<<<a.scan_tiles, kScanThreads, 0, st>>>(a);
   if (a.n > 0) {
-    int grid = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
-    scatter_kernel<<<grid, 256, 0, st>>>(a);
+    // the radix kernels return at once when the input is grouped by cell
+    int grid = (int)std::min<int64_t>((a.n + kRadixThreads - 1) / kRadixThreads, (int64_t)sms * 4);
+    radix_prep_kernel<<<grid, kRadixThreads, 0, st>>>(a);
+    for (int p = 0; p < a.radix_passes; ++p)
+      radix_pass_kernel<<<radix_tiles_for(a.n), kRadixThreads, 0, st>>>(a, p);
   }
   return cudaGetLastError();
 }

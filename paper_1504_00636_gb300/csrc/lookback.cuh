@@ -33,18 +33,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Called by one thread of the tile; returns the exclusive prefix of `tile`.
+// The status word of tile t is status[t * stride] (several independent scans
+// can interleave their words).
 __device__ inline long long tile_exclusive_prefix(unsigned long long *status, int tile,
-                                                  long long aggregate, unsigned *err) {
+                                                  long long aggregate, unsigned *err,
+                                                  int stride = 1) {
   if (tile == 0) {
     st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
     return 0;
   }
-  st_release_u64(&status[tile], kFlagAgg | (unsigned long long)aggregate);
+  st_release_u64(&status[(size_t)tile * stride], kFlagAgg | (unsigned long long)aggregate);
   long long prefix = 0;
   int t = tile - 1;
   unsigned long long t0 = 0;
   while (t >= 0) {
-    unsigned long long s = ld_acquire_u64(&status[t]);
+    unsigned long long s = ld_acquire_u64(&status[(size_t)t * stride]);
     unsigned long long f = s >> 62;
     if (f == 0) {
       unsigned long long now = global_ns();
@@ -61,7 +64,8 @@ __device__ inline long long tile_exclusive_prefix(unsigned long long *status, in
     if (f == 2) break;
     --t;
   }
-  st_release_u64(&status[tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+  st_release_u64(&status[(size_t)tile * stride],
+                 kFlagInc | (unsigned long long)(prefix + aggregate));
   return prefix;
 }
 

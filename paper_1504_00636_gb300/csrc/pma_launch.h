@@ -26,7 +26,6 @@ struct BinArgs {
   int32_t n_min;
   int32_t *counts;      // [n_cells]
   int32_t *cell_begin;  // [n_cells + 1]
-  int32_t *fill;        // [n_cells]
   int32_t *perm;        // [n]
   int32_t *unsorted;    // device flag
   int32_t *big_list;
@@ -40,9 +39,25 @@ struct BinArgs {
   unsigned long long *scan_status;  // [scan tiles]
   int32_t *scan_ticket;
   int32_t scan_tiles;
+  // stable LSD radix sort of ungrouped input by cell id (Step 1)
+  int32_t radix_passes;             // <= kRadixMaxPasses
+  int32_t radix_shift[4];           // first key bit of each pass
+  int32_t radix_bits[4];            // key bits of each pass (<= 8)
+  int32_t radix_tiles;              // tiles of kRadixTile keys
+  int32_t *radix_count;             // [kRadixMaxPasses][256] digit counts (zeroed by the caller)
+  int32_t *radix_ticket;            // [kRadixMaxPasses] tile tickets (zeroed by the caller)
+  unsigned long long *radix_status; // [2][radix_tiles][256] look-back words
+  int32_t *radix_keys[2];           // [n] intermediate keys
+  int32_t *radix_vals[2];           // [n] intermediate input indices
 };
+constexpr int kRadixMaxPasses = 4;
+constexpr int kRadixBins = 256;
 cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st);
 int scan_tiles_for(int64_t n);
+int radix_tiles_for(int64_t n);
+// passes and bit split of the cell-id keys (values 0..n_cells, n_cells marks
+// an invalid id); fills a.radix_passes / radix_shift / radix_bits
+void radix_plan(BinArgs &a);
 
 // emit.cu
 struct EmitArgs {

@@ -1,4 +1,6 @@
 """CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -82,6 +84,14 @@ def test_fp64_big_cells_take_the_global_path():
     assert g["stats"]["big_cells"] >= 2
     compare(p, g, _oracle(p))
     conservation(p, g)
+    # the same cells, ungrouped: sorted stably, so the result is unchanged
+    x = p.shuffled(4)
+    y, order = _grouped(x)
+    gx, gy = run_gpu(x, "fp64"), run_gpu(y, "fp64")
+    assert gx["stats"]["sorted_input"] == 0 and gx["stats"]["big_cells"] >= 2
+    for key in ("cell", "pos", "mom", "w"):
+        np.testing.assert_array_equal(gx[key], gy[key])
+    np.testing.assert_array_equal(gx["index"][order], gy["index"])
 
 
 def test_fp64_shuffled_input():
@@ -90,6 +100,61 @@ def test_fp64_shuffled_input():
     assert g["stats"]["sorted_input"] == 0
     compare(p, g, _oracle(p))
     conservation(p, g)
+
+
+def _grouped(x):
+    """The same particles grouped by cell, keeping input order inside a cell
+    (Step 1's order), and the permutation used."""
+    order = np.argsort(x.cell, kind="stable")
+    y = dataclasses.replace(x, name=x.name + "_grouped", cell=x.cell[order],
+                            pos=np.ascontiguousarray(x.pos[:, order]),
+                            mom=np.ascontiguousarray(x.mom[:, order]),
+                            w=np.ascontiguousarray(x.w[order]))
+    return y, order
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("make", [
+    lambda: synth.two_stream(cells=64).shuffled(5),
+    lambda: synth.shower(grid=(40, 40), cap=3000).shuffled(6),
+], ids=["two_stream_64", "shower_40x40"])
+def test_ungrouped_input_sorts_stably(make, precision):
+    # ungrouped input is sorted by (cell, input index): the result equals the
+    # run on the grouped copy bit for bit, and repeats exactly
+    x = make()
+    if precision == "mixed":
+        x = x.astype(np.float32)
+    y, order = _grouped(x)
+    gx, gx2, gy = run_gpu(x, precision), run_gpu(x, precision), run_gpu(y, precision)
+    assert gx["stats"]["sorted_input"] == 0 and gy["stats"]["sorted_input"] == 1
+    for key in ("cell", "pos", "mom", "w"):
+        np.testing.assert_array_equal(gx[key], gy[key])
+        np.testing.assert_array_equal(gx[key], gx2[key])
+    np.testing.assert_array_equal(gx["index"][order], gy["index"])
+    if precision == "fp64":
+        compare(x, gx, _oracle(x))
+
+
+def test_ungrouped_input_many_cells():
+    # 2^18 + 3 cells need three 7-bit radix passes; most cells hold 0-3
+    # particles; a few ids repeat far apart in the input
+    rng = np.random.default_rng(11)
+    n_cells, n = (1 << 18) + 3, 400_000
+    cell = rng.integers(0, n_cells, n).astype(np.int32)
+    cell[rng.integers(0, n, 2000)] = n_cells - 1
+    pos = (rng.random((2, n)) + 0.0)
+    mom = rng.normal(0.2, 0.05, size=(3, n))
+    w = rng.lognormal(0.0, 0.5, size=n)
+    x = synth.Particles("many_cells", 2, 3, n_cells, (1.0, 1.0, 1.0), 0.05, 0.05, 0,
+                        cell, pos, mom, w)
+    y, order = _grouped(x)
+    gx, gy = run_gpu(x, "fp64"), run_gpu(y, "fp64")
+    assert gx["stats"]["sorted_input"] == 0
+    for key in ("cell", "pos", "mom", "w"):
+        np.testing.assert_array_equal(gx[key], gy[key])
+    np.testing.assert_array_equal(gx["index"][order], gy["index"])
+    compare(x, gx, _oracle(x))
+    conservation(x, gx)
 
 
 def test_fp64_n_min_passthrough():
