@@ -78,7 +78,8 @@ struct pma_handle {
   unsigned long long *radix_status = nullptr;
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
   int32_t *warp_list = nullptr, *block_list = nullptr;
-  void *fin = nullptr;  // staging: D + 1 columns of capacity entries
+  void *fin = nullptr;  // staging: D + 1 columns of fin_stride entries
+  int64_t fin_stride = 0;  // capacity rounded up to 16 entries (bulk-copy alignment)
   uint8_t *head = nullptr;
   unsigned long long *bin_status = nullptr;
   int32_t *tile_count = nullptr;
@@ -236,15 +237,16 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->radix_count, kRadixMaxPasses * kRadixBins) == cudaSuccess &&
             dalloc(&h->radix_status, (size_t)2 * radix_tiles_for(N) * kRadixBins) == cudaSuccess &&
             dalloc(&h->perm, N) == cudaSuccess &&
-            dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, N) == cudaSuccess &&
+            dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, Npad) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
-            cudaMalloc(&h->fin, (size_t)N * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
+            cudaMalloc(&h->fin, (size_t)Npad * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->tile_count, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->tile_prefix, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
             cudaMallocHost(reinterpret_cast<void **>(&h->ctl_host), sizeof(Ctl)) == cudaSuccess;
+  h->fin_stride = Npad;
   if (!ok) {
     cudaGetLastError();
     free_all(h);
@@ -329,7 +331,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
     // Step 1), intermediate indices in the two spare permutation arrays
     const size_t es = h->mixed ? 4 : 8;
     b.radix_keys[0] = reinterpret_cast<int32_t *>(h->fin);
-    b.radix_keys[1] = reinterpret_cast<int32_t *>(static_cast<char *>(h->fin) + (size_t)h->capacity * es);
+    b.radix_keys[1] = reinterpret_cast<int32_t *>(static_cast<char *>(h->fin) + (size_t)h->fin_stride * es);
     b.radix_vals[0] = h->perm_tmp;
     b.radix_vals[1] = h->perm_final;
   }
@@ -362,7 +364,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   {
     const size_t es = h->mixed ? 4 : 8;
     for (int l = 0; l <= h->D; ++l)
-      P.fin[l] = static_cast<char *>(h->fin) + (size_t)l * h->capacity * es;
+      P.fin[l] = static_cast<char *>(h->fin) + (size_t)l * h->fin_stride * es;
   }
   P.cell_begin = h->cell_begin;
   P.perm = h->perm;

@@ -9,7 +9,9 @@
 //   tiles_kernel   exclusive prefix over tiles (one CTA) and the count M
 //   emit_kernel    per tile: slots, merged particles, input -> output index;
 //                  a merged set's centroid (W, X, P) is an FP64 sum over its
-//                  staged members (a product of two floats is exact in FP64)
+//                  staged members (a product of two floats is exact in FP64).
+//                  The tile's staged columns reach shared memory by bulk
+//                  asynchronous copies while the CTA scans the head bytes.
 #include "lookback.cuh"
 #include "pma_launch.h"
 
@@ -90,8 +92,71 @@ __global__ void __launch_bounds__(kScanCta) tiles_kernel(EmitArgs a) {
   }
 }
 
+// ---- bulk asynchronous copies global -> shared, completed on an mbarrier
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// dst and src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// waits at most limit_ns; true when the phase completed
+__device__ inline bool mbar_wait(uint64_t *bar, unsigned phase, unsigned long long limit_ns) {
+  unsigned long long t0 = 0;
+  while (!mbar_try_wait(bar, phase)) {
+    const unsigned long long now = global_ns();
+    if (t0 == 0)
+      t0 = now;
+    else if (now - t0 > limit_ns)
+      return false;
+  }
+  return true;
+}
+
+size_t emit_smem_bytes(int D, int mixed) {
+  return (size_t)(D + 1) * kEmitTile * (mixed ? 4 : 8) + (size_t)kEmitTile * 4;
+}
+
+// One CTA per tile of 1024 final positions.  One thread starts bulk copies of
+// the tile's staged columns and final permutation into shared memory; the
+// CTA meanwhile reads the head bytes and scans them into output slots.  The
+// positions are then handled in consecutive order across the threads, so the
+// output stores of runs of one-particle sets are coalesced.
 template <typename T>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_warp[32];
   __shared__ unsigned short s_mask[kEmitThreads];
   __shared__ int s_chunk[kEmitThreads];
@@ -99,93 +164,97 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   __shared__ int s_nmerged;
   __shared__ int2 s_merged[kEmitTile / 2 + 1];  // (offset in tile, output slot)
   const int tid = threadIdx.x;
-  if (tid == 0) s_nmerged = 0;
+  const int D = a.dx + a.dp;
   const int64_t t0 = (int64_t)blockIdx.x * kEmitTile;
+  const int cnt = (int)(a.n - t0 < (int64_t)kEmitTile ? a.n - t0 : (int64_t)kEmitTile);
+  T *s_col = reinterpret_cast<T *>(s_dyn);  // column l at s_col[l * kEmitTile]
+  int32_t *s_perm = reinterpret_cast<int32_t *>(s_dyn + (size_t)(D + 1) * kEmitTile * sizeof(T));
+  if (tid == 0) {
+    s_nmerged = 0;
+    mbar_init(&s_bar, 1);
+    // the staging columns and perm_final hold a multiple of 16 entries, so
+    // the rounded-up tail stays inside their allocations
+    const unsigned cb = ((unsigned)cnt * (unsigned)sizeof(T) + 15u) & ~15u;
+    const unsigned pb = ((unsigned)cnt * 4u + 15u) & ~15u;
+    mbar_expect_tx(&s_bar, cb * (unsigned)(D + 1) + pb);
+    for (int l = 0; l <= D; ++l)
+      bulk_copy_g2s(s_col + (size_t)l * kEmitTile, static_cast<const T *>(a.fin[l]) + t0, cb,
+                    &s_bar);
+    bulk_copy_g2s(s_perm, a.perm_final + t0, pb, &s_bar);
+  }
   const unsigned hw = load_heads(a.head, t0 + (int64_t)tid * kEmitChunk, a.n);
   const unsigned mask = head_mask(hw);
   reinterpret_cast<unsigned *>(s_head)[tid] = hw;
   int total;
-  const int ex = block_exclusive_scan(__popc(mask), s_warp, &total);
+  const int ex = block_exclusive_scan(__popc(mask), s_warp, &total);  // barriers: s_bar is set up
   s_mask[tid] = (unsigned short)mask;
   s_chunk[tid] = ex;
-  __syncthreads();
   const long long prefix = a.tile_prefix[blockIdx.x];
-  const int32_t *__restrict__ perm_final = a.perm_final;
-  const int32_t *__restrict__ cells = a.cells;
   const bool sorted = *a.unsorted == 0;
-  const int D = a.dx + a.dp;
+  const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0, kWaitNs));
+  if (late) {
+    // never leave with copies in flight into this CTA's shared memory
+    if (tid == 0) atomicOr(a.err, kErrTimeout);
+    mbar_wait(&s_bar, 0, kWaitNs);
+    return;
+  }
   bool bad = false, internal = false;
-  // positions in strided order (consecutive threads, consecutive positions);
-  // all loads of a thread's positions are issued before its stores
-  int orig[kEmitChunk], hh[kEmitChunk], cc[kEmitChunk];
-  long long slot[kEmitChunk];
-  T xv[kEmitChunk][kMaxD + 1];
 #pragma unroll
   for (int j = 0; j < kEmitChunk; ++j) {
     const int off = j * kEmitThreads + tid;
-    const int64_t p = t0 + off;
-    orig[j] = -1;
-    hh[j] = -1;  // beyond n
-    cc[j] = 0;
-    slot[j] = 0;
-#pragma unroll
-    for (int l = 0; l <= kMaxD; ++l) xv[j][l] = T(1);
-    if (p < a.n) {
-      const int ch = off / kEmitChunk, in = off % kEmitChunk;
-      const unsigned m = s_mask[ch];
-      slot[j] = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
-      orig[j] = perm_final[p];
-      hh[j] = s_head[off];
-      if (hh[j]) {
-        cc[j] = cells[sorted ? p : (int64_t)max(orig[j], 0)];
-        if (hh[j] == kHeadSingle) {
-#pragma unroll
-          for (int l = 0; l <= kMaxD; ++l)
-            if (l <= D) xv[j][l] = static_cast<const T *>(a.fin[l])[p];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kEmitChunk; ++j) {
-    if (hh[j] < 0) continue;
-    if ((unsigned)orig[j] >= (unsigned)a.n) {
+    if (off >= cnt) break;
+    const int ch = off / kEmitChunk, in = off % kEmitChunk;
+    const unsigned m = s_mask[ch];
+    const long long slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
+    const int orig = s_perm[off];
+    const int h = s_head[off];
+    if ((unsigned)orig >= (unsigned)a.n) {
       // a position left unwritten by an earlier failure: never follow it
       internal = true;
       continue;
     }
-    if (a.out_index) a.out_index[orig[j]] = (int32_t)slot[j];
-    if (!hh[j]) continue;
-    a.out_cell[slot[j]] = cc[j];
-    if (hh[j] == kHeadSingle) {
+    if (a.out_index) a.out_index[orig] = (int32_t)slot;
+    if (!h) continue;
+    a.out_cell[slot] = a.cells[sorted ? t0 + off : (int64_t)orig];
+    if (h == kHeadSingle) {
       // one-particle set: the particle itself (Step 7)
-      for (int l = 0; l < a.dx; ++l) {
-        bad |= !isfinite(xv[j][l]);
-        static_cast<T *>(a.out_pos[l])[slot[j]] = xv[j][l];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        if (l < a.dx) {
+          const T v = s_col[l * kEmitTile + off];
+          bad |= !isfinite(v);
+          static_cast<T *>(a.out_pos[l])[slot] = v;
+        }
       }
-      for (int l = 0; l < a.dp; ++l) {
-        bad |= !isfinite(xv[j][a.dx + l]);
-        a.out_mom[l][slot[j]] = to_f64<T>(xv[j][a.dx + l]);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        if (l < a.dp) {
+          const T v = s_col[(a.dx + l) * kEmitTile + off];
+          bad |= !isfinite(v);
+          a.out_mom[l][slot] = to_f64<T>(v);
+        }
       }
-      const T w = xv[j][D];
+      const T w = s_col[D * kEmitTile + off];
       bad |= !(w > T(0)) || !isfinite(w);
-      a.out_w[slot[j]] = to_f64<T>(w);
+      a.out_w[slot] = to_f64<T>(w);
     } else {
       // merged set: summed below, densely, by the whole CTA
       const int k = atomicAdd(&s_nmerged, 1);
-      s_merged[k] = make_int2(j * kEmitThreads + tid, (int)slot[j]);
+      s_merged[k] = make_int2(off, (int)slot);
     }
   }
   __syncthreads();
   for (int k = tid; k < s_nmerged; k += kEmitThreads) {
-    const int64_t p = t0 + s_merged[k].x;
+    const int off = s_merged[k].x;
     const long long slot_m = s_merged[k].y;
-    const int h = s_head[s_merged[k].x];
+    const int h = s_head[off];
     // members: the head's count, or (255) every position up to the next head
-    int64_t e = p + h;
+    int64_t e = t0 + off + h;
     if (h == kHeadLong) {
-      e = p + 1;
-      while (e < a.n && a.head[e] == 0) ++e;
+      e = t0 + off + 1;
+      while (e < t0 + cnt && s_head[e - t0] == 0) ++e;
+      if (e == t0 + cnt)
+        while (e < a.n && a.head[e] == 0) ++e;
     }
     if (e > a.n) {
       internal = true;
@@ -194,31 +263,65 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     double W = 0.0, S1[kMaxD];
 #pragma unroll
     for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
-    for (int64_t r = p; r < e; ++r) {
-      const double w = to_f64<T>(static_cast<const T *>(a.fin[D])[r]);
-      W += w;
+    if (e <= t0 + cnt) {
+      // the whole set lies in this tile
+      for (int r = off; r < (int)(e - t0); ++r) {
+        const double w = to_f64<T>(s_col[D * kEmitTile + r]);
+        W += w;
 #pragma unroll
-      for (int l = 0; l < kMaxD; ++l)
-        if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.fin[l])[r]), S1[l]);
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) S1[l] = fma(w, to_f64<T>(s_col[l * kEmitTile + r]), S1[l]);
+      }
+    } else {
+      for (int64_t r = t0 + off; r < e; ++r) {
+        const double w = to_f64<T>(static_cast<const T *>(a.fin[D])[r]);
+        W += w;
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.fin[l])[r]), S1[l]);
+      }
     }
     const double inv = 1.0 / W;
     a.out_w[slot_m] = W;
-    for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot_m] = (T)(S1[l] * inv);
-    for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot_m] = S1[a.dx + l] * inv;
+#pragma unroll
+    for (int l = 0; l < kMaxD; ++l) {
+      if (l < D) {
+        const double v = S1[l] * inv;
+        if (l < 3 && l < a.dx)
+          static_cast<T *>(a.out_pos[l])[slot_m] = (T)v;
+        else
+          a.out_mom[l - a.dx][slot_m] = v;
+      }
+    }
   }
   if (bad) atomicOr(a.err, kErrInput);
   if (internal) atomicOr(a.err, kErrInternal);
+}
+
+template <typename T>
+static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
+  const size_t smem = emit_smem_bytes(a.dx + a.dp, sizeof(T) == 4);
+  // raise the dynamic shared-memory limit once per device
+  static int limit_set[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
+    e = cudaFuncSetAttribute(emit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
+  }
+  emit_kernel<T><<<a.tiles, kEmitThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
   if (a.tiles <= 0) return cudaSuccess;
   count_kernel<<<a.tiles, kEmitThreads, 0, st>>>(a);
   tiles_kernel<<<1, kScanCta, 0, st>>>(a);
-  if (a.mixed)
-    emit_kernel<float><<<a.tiles, kEmitThreads, 0, st>>>(a);
-  else
-    emit_kernel<double><<<a.tiles, kEmitThreads, 0, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = a.mixed ? launch_emit_t<float>(a, st) : launch_emit_t<double>(a, st);
+  return e;
 }
 
 }  // namespace pma
