@@ -38,10 +38,12 @@ __device__ __forceinline__ int size_class(int m) {
   return 6;
 }
 
-// most subsets of a class that can be pending at once (they are disjoint)
+// most subsets of a class that can be pending at once: they are disjoint
+// subsets of at least lo particles of one tile of at most cap
 __host__ __device__ inline int class_capacity(int c, int cap) {
-  const int lo[kClasses] = {2, 3, 13, 25, 49, 97, 193};
-  return cap / lo[c] + 1;
+  // smallest size of class c: 2, 3, 13, 25, 49, 97, 193
+  const int lo = c == 0 ? 2 : (c == 1 ? 3 : (12 << (c - 2)) + 1);
+  return cap / lo;
 }
 
 __host__ __device__ inline int stacks_entries(int cap) {
@@ -58,21 +60,28 @@ __device__ __forceinline__ int rec_begin(uint32_t r) { return (int)(r & 8191u); 
 __device__ __forceinline__ int rec_len(uint32_t r) { return (int)((r >> 13) & 8191u); }
 __device__ __forceinline__ int rec_par(uint32_t r) { return (int)((r >> 26) & 1u); }
 
+// Views into the tile's shared memory.  Every member is a plain pointer or
+// integer (no arrays), so the struct lives in registers.
 template <typename T, int D>
 struct WarpTile {
-  T *data;           // [D + 1][cap]: coordinates, then weight
-  uint16_t *idx[2];  // index arrays, by depth parity
-  uint32_t *stk[kClasses];
-  int *top;          // [kClasses]
+  T *data;         // [D + 1][cap]: coordinates, then weight
+  uint16_t *idx0;  // [2][cap] index arrays, by depth parity
+  uint32_t *stk0;  // the class stacks, back to back
+  int *top;        // [kClasses] stack heights
+  uint16_t *soff;  // [kClasses] first entry of each stack, [kClasses] capacities
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
+  __device__ __forceinline__ uint16_t *idx(int par) const { return idx0 + par * cap; }
+  __device__ __forceinline__ uint32_t *stk(int c) const { return stk0 + soff[c]; }
+  __device__ __forceinline__ int stk_cap(int c) const { return soff[kClasses + c]; }
 };
 
 template <typename T, int D>
 __host__ __device__ inline size_t warp_region_bytes(int cap) {
   size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
-  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 4) * sizeof(int);
+  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 1) * sizeof(int) +
+       2 * kClasses * sizeof(uint16_t);
   return (b + 15) & ~size_t(15);
 }
 
@@ -88,12 +97,20 @@ __device__ __forceinline__ void stage(const Problem &P, const WarpTile<T, D> &S,
   for (int l = 0; l <= D; ++l) static_cast<T *>(P.fin[l])[gp] = S.col(l)[j];
 }
 
+// A final set's positions [b, b + m) belong to no other subset, so both
+// index buffers are free there: buffer 0 takes the tile index of the particle
+// at each final position and buffer 1 its head code (Step 7 input); the unit
+// is written out to global memory in one coalesced pass at its end.
 template <typename T, int D>
-__device__ __forceinline__ void emit_single(const Problem &P, const WarpTile<T, D> &S,
-                                            const int32_t *perm, int64_t gb, int pos, int j) {
-  P.perm_final[gb + pos] = orig_index(perm, gb, j);
-  P.head[gb + pos] = kHeadSingle;
-  stage<T, D>(P, S, gb + pos, j);
+__device__ __forceinline__ void mark_final(const WarpTile<T, D> &S, int pos, int j, int h) {
+  S.idx(0)[pos] = (uint16_t)j;
+  S.idx(1)[pos] = (uint16_t)h;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void emit_single(const Problem &, const WarpTile<T, D> &S,
+                                            const int32_t *, int64_t, int pos, int j) {
+  mark_final<T, D>(S, pos, j, kHeadSingle);
 }
 
 template <typename T, int D>
@@ -101,14 +118,14 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
                                            const int32_t *perm, int64_t gb, int b, int m,
                                            int par, Counters &cnt) {
   if (m == 1) {
-    emit_single<T, D>(P, S, perm, gb, b, S.idx[par][b]);
+    emit_single<T, D>(P, S, perm, gb, b, S.idx(par)[b]);
     cnt.leaves += 1;
     return;
   }
   const int c = size_class(m);
   const int slot = atomicAdd(&S.top[c], 1);
-  if (slot < class_capacity(c, S.cap))
-    S.stk[c][slot] = pack_rec(b, m, par);
+  if (slot < S.stk_cap(c))
+    S.stk(c)[slot] = pack_rec(b, m, par);
   else
     set_error(P.err, kErrInternal);
 }
@@ -121,13 +138,13 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   const int lg = c - 1, G = 1 << lg;
   const int gid = lane >> lg, gl = lane & (G - 1);
   const bool act = gid < kw;
-  const uint32_t rec = act ? S.stk[c][base - gid] : 0u;
+  const uint32_t rec = act ? S.stk(c)[base - gid] : 0u;
   const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
 
   // Steps 1-2: moments about the set's first particle
   T s[D];
   {
-    const int j0 = act ? S.idx[par][b] : 0;
+    const int j0 = act ? S.idx(par)[b] : 0;
 #pragma unroll
     for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
   }
@@ -135,7 +152,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   M.zero();
 #pragma unroll 4
   for (int i = gl; i < m; i += G) {
-    const int j = S.idx[par][b + i];
+    const int j = S.idx(par)[b + i];
     T q[D];
 #pragma unroll
     for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
@@ -160,9 +177,9 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
     if (split)
 #pragma unroll 4
       for (int i = 0; i < m; ++i) {
-        const int j = S.idx[par][b + i];
+        const int j = S.idx(par)[b + i];
         const int dst = Decider<T, D>::left(qk[j], cut) ? (b + cntL++) : (b + m - 1 - cntR++);
-        S.idx[np][dst] = (uint16_t)j;
+        S.idx(np)[dst] = (uint16_t)j;
       }
   } else {
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
@@ -171,14 +188,14 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
     for (int base = 0; base < mmax; base += G) {
       const int i = base + gl;
       const bool valid = split && i < m;
-      const int j = valid ? S.idx[par][b + i] : 0;
+      const int j = valid ? S.idx(par)[b + i] : 0;
       const bool lft = valid && Decider<T, D>::left(qk[j], cut);
       const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
       const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
       if (valid) {
         const int dst =
             lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
-        S.idx[np][dst] = (uint16_t)j;
+        S.idx(np)[dst] = (uint16_t)j;
       }
       cntL += __popc(bl);
       cntR += __popc(br);
@@ -188,15 +205,11 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   const bool degenerate = split && (cntL == 0 || cntR == 0);
   const bool final_set = act && (cut.leaf || degenerate);
   const int epar = cut.leaf ? par : np;
-  // final sets: permutation and head bytes (Step 7 sums them up later)
+  // final sets: final order and head codes (Step 7 sums them up later)
   if (final_set) {
-    const uint8_t h = head_code(m);
-    for (int i = gl; i < m; i += G) {
-      const int j = S.idx[epar][b + i];
-      P.perm_final[gb + b + i] = orig_index(perm, gb, j);
-      P.head[gb + b + i] = (i == 0) ? h : (uint8_t)0;
-      stage<T, D>(P, S, gb + b + i, j);
-    }
+    const int h = head_code(m);
+    for (int i = gl; i < m; i += G)
+      mark_final<T, D>(S, b + i, S.idx(epar)[b + i], i == 0 ? h : 0);
   }
   if (gl == 0 && act) {
     if (final_set) {
@@ -218,10 +231,10 @@ template <typename T, int D>
 __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
                            int64_t gb, int lane, Counters &cnt, int kw, int base) {
   const bool act = lane < kw;
-  const uint32_t rec = act ? S.stk[0][base - lane] : 0u;
+  const uint32_t rec = act ? S.stk(0)[base - lane] : 0u;
   if (!act) return;
   const int b = rec_begin(rec), par = rec_par(rec);
-  const int ja = S.idx[par][b], jb = S.idx[par][b + 1];
+  const int ja = S.idx(par)[b], jb = S.idx(par)[b + 1];
   T qa[D], qb[D];
 #pragma unroll
   for (int l = 0; l < D; ++l) {
@@ -254,17 +267,13 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
       second = ja;
     }
   }
-  P.perm_final[gb + b] = orig_index(perm, gb, first);
-  P.perm_final[gb + b + 1] = orig_index(perm, gb, second);
-  stage<T, D>(P, S, gb + b, first);
-  stage<T, D>(P, S, gb + b + 1, second);
   if (merged) {
-    P.head[gb + b] = kHeadMerged;
-    P.head[gb + b + 1] = 0;
+    mark_final<T, D>(S, b, first, kHeadMerged);
+    mark_final<T, D>(S, b + 1, second, 0);
     cnt.leaves += 1;
   } else {
-    P.head[gb + b] = kHeadSingle;
-    P.head[gb + b + 1] = kHeadSingle;
+    mark_final<T, D>(S, b, first, kHeadSingle);
+    mark_final<T, D>(S, b + 1, second, kHeadSingle);
     cnt.leaves += 2;
     cnt.splits += 1;
     cnt.depth += 2;
@@ -309,19 +318,21 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
   {
     unsigned char *base = smem_raw;
     S.data = reinterpret_cast<T *>(base);
-    S.idx[0] = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
-    S.idx[1] = S.idx[0] + cap;
+    S.idx0 = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
     const size_t off =
         ((size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t) + 15) &
         ~size_t(15);
-    uint32_t *st = reinterpret_cast<uint32_t *>(base + off);
-    for (int c = 0; c < kClasses; ++c) {
-      S.stk[c] = st;
-      st += class_capacity(c, cap);
-    }
-    S.top = reinterpret_cast<int *>(st);
+    S.stk0 = reinterpret_cast<uint32_t *>(base + off);
+    S.top = reinterpret_cast<int *>(S.stk0 + stacks_entries(cap));
     ctl = S.top + kClasses;
+    S.soff = reinterpret_cast<uint16_t *>(ctl + 1);
     S.cap = cap;
+    if (tt < kClasses) {
+      int o = 0;
+      for (int c = 0; c < tt; ++c) o += class_capacity(c, cap);
+      S.soff[tt] = (uint16_t)o;
+      S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap);
+    }
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
   const int count = *U.count;
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
         const T w = StoreOf<T>::load(P.w, src);
         bad |= !(w > T(0)) || !finite_val(w);
         S.col(D)[i] = w;
-        S.idx[0][i] = (uint16_t)i;
+        S.idx(0)[i] = (uint16_t)i;
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
       if (tt < kClasses) S.top[tt] = 0;
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
           cnt.leaves += 1;
         } else {
           const int c = size_class(n);
-          S.stk[c][0] = pack_rec(0, n, 0);
+          S.stk(c)[0] = pack_rec(0, n, 0);
           S.top[c] = 1;
         }
       }
@@ -430,6 +441,21 @@ __global__ void __launch_bounds__(32 * TEAM) team_kernel(Problem P, UnitSource U
         }
         __syncwarp();
       }
+      // the unit in final order: permutation, head bytes, staged particles
+      for (int i = tt; i < n; i += kThreads) {
+        const int j = S.idx(0)[i];
+        if (j >= n) {
+          // only after an internal failure left a position unmarked
+          set_error(P.err, kErrInternal);
+          P.perm_final[gb + i] = -1;
+          P.head[gb + i] = 0;
+          continue;
+        }
+        P.perm_final[gb + i] = orig_index(perm, gb, j);
+        P.head[gb + i] = (uint8_t)S.idx(1)[i];
+        stage<T, D>(P, S, gb + i, j);
+      }
+      __syncthreads();
     }
   }
 #pragma unroll
