@@ -32,6 +32,12 @@ NEAR_STOP = 1
 NEAR_ARGMAX = 2
 NEAR_CUT = 4
 
+# decision variants (bit flags), off by default:
+# VAR_NORMALIZED  Step 4 maximises Delta_l / T_l instead of the raw Delta_l
+# VAR_PNORM       momentum CVs use |P| (length of the mean momentum vector)
+VAR_NORMALIZED = 2
+VAR_PNORM = 4
+
 _ERRORS = {1: "invalid argument", 2: "invalid input", 3: "out of memory"}
 
 
@@ -66,13 +72,14 @@ def load_library(path):
     i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     lib.pma_oracle_merge.argtypes = [i64, P, ctypes.c_int, ctypes.c_int, P, P, P,
                                      i64, P, i32, dbl, dbl, ctypes.c_int,
-                                     P, P, P, P, P, P, P, ctypes.POINTER(_Stats)]
+                                     P, P, P, P, P, P, P, ctypes.POINTER(_Stats),
+                                     ctypes.c_uint]
     lib.pma_oracle_merge.restype = ctypes.c_int
     lib.pma_oracle_trace.argtypes = [i64, ctypes.c_int, ctypes.c_int, P, P, P, P,
-                                     dbl, dbl, P, P, P, P, P, P, P, P]
+                                     dbl, dbl, P, P, P, P, P, P, P, P, ctypes.c_uint]
     lib.pma_oracle_trace.restype = ctypes.c_int
     lib.pma_oracle_subset_moments.argtypes = [i64, ctypes.c_int, ctypes.c_int, P, P,
-                                              i64, P, P, P, P, P, P, P]
+                                              i64, P, P, P, P, P, P, P, ctypes.c_uint]
     lib.pma_oracle_subset_moments.restype = ctypes.c_int
     return lib
 
@@ -109,7 +116,7 @@ class MergeResult:
 
 
 def merge(cell, pos, mom, w, n_cells, cell_size=(1.0, 1.0, 1.0), n_min=0,
-          tol_x=0.1, tol_p=0.1, threads=1, lib=None) -> MergeResult:
+          tol_x=0.1, tol_p=0.1, threads=1, lib=None, variant=0) -> MergeResult:
     """Merge every cell (Steps 1-7); inputs are upcast to float64."""
     lib = _load(lib)
     cell = np.ascontiguousarray(cell, dtype=np.int32)
@@ -132,7 +139,7 @@ def merge(cell, pos, mom, w, n_cells, cell_size=(1.0, 1.0, 1.0), n_min=0,
                               int(n_cells), _ptr(cs), int(n_min), float(tol_x), float(tol_p),
                               int(threads), _ptr(out_cell), _ptr(out_pos), _ptr(out_mom),
                               _ptr(out_w), _ptr(out_index), _ptr(flags),
-                              ctypes.byref(count), ctypes.byref(st))
+                              ctypes.byref(count), ctypes.byref(st), int(variant))
     if rc != 0:
         raise ValueError("oracle merge failed: %s" % _ERRORS.get(rc, rc))
     m = count.value
@@ -142,12 +149,13 @@ def merge(cell, pos, mom, w, n_cells, cell_size=(1.0, 1.0, 1.0), n_min=0,
                        flags, stats)
 
 
-def merge_particles(p, threads=1, tol_x=None, tol_p=None, n_min=None, lib=None) -> MergeResult:
+def merge_particles(p, threads=1, tol_x=None, tol_p=None, n_min=None, lib=None,
+                    variant=0) -> MergeResult:
     """``merge`` on a ``synth.Particles`` set."""
     return merge(p.cell, p.pos, p.mom, p.w, p.n_cells, p.cell_size,
                  p.n_min if n_min is None else n_min,
                  p.tol_x if tol_x is None else tol_x,
-                 p.tol_p if tol_p is None else tol_p, threads, lib=lib)
+                 p.tol_p if tol_p is None else tol_p, threads, lib=lib, variant=variant)
 
 
 @dataclasses.dataclass
@@ -161,7 +169,8 @@ class Trace:
     near: int
 
 
-def trace(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1, lib=None) -> Trace:
+def trace(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1, lib=None,
+          variant=0) -> Trace:
     """The recursion tree of one particle set (one cell), V1-first preorder."""
     lib = _load(lib)
     pos, mom, w = _f64(pos), _f64(mom), _f64(w)
@@ -176,7 +185,7 @@ def trace(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1, lib=None
     rc = lib.pma_oracle_trace(m, pos.shape[0], mom.shape[0], _ptr(pos), _ptr(mom), _ptr(w),
                               _ptr(cs), float(tol_x), float(tol_p), _ptr(perm), _ptr(nb),
                               _ptr(ne), _ptr(nd), _ptr(na), _ptr(nq), ctypes.byref(nn),
-                              ctypes.byref(near))
+                              ctypes.byref(near), int(variant))
     if rc != 0:
         raise ValueError("oracle trace failed: %s" % _ERRORS.get(rc, rc))
     k = nn.value
@@ -184,7 +193,7 @@ def trace(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1, lib=None
                  nq[:k].copy(), near.value)
 
 
-def subset_moments(pos, mom, w, cell_size=(1.0, 1.0, 1.0), idx=None, lib=None):
+def subset_moments(pos, mom, w, cell_size=(1.0, 1.0, 1.0), idx=None, lib=None, variant=0):
     """Steps 1-2 on one set: returns (W, Q[D], sigma[D], Delta[D])."""
     lib = _load(lib)
     pos, mom, w = _f64(pos), _f64(mom), _f64(w)
@@ -197,7 +206,7 @@ def subset_moments(pos, mom, w, cell_size=(1.0, 1.0, 1.0), idx=None, lib=None):
     mm = m if ix is None else ix.shape[0]
     rc = lib.pma_oracle_subset_moments(mm, pos.shape[0], mom.shape[0], _ptr(pos), _ptr(mom),
                                        m, _ptr(w), _ptr(ix), _ptr(cs), ctypes.byref(W),
-                                       _ptr(Q), _ptr(S), _ptr(Dl))
+                                       _ptr(Q), _ptr(S), _ptr(Dl), int(variant))
     if rc != 0:
         raise ValueError("oracle moments failed: %s" % _ERRORS.get(rc, rc))
     return W.value, Q, S, Dl

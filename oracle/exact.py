@@ -13,6 +13,11 @@ roots are avoided by comparing squares of non-negative quantities:
   P == 0 < var), lowest axis on exact ties.
 * Step 5: q <= Q exactly.
 
+Variants (the bits of ``variant``, as in the C oracle): ``VAR_NORMALIZED``
+maximises (Delta_l / T_l)^2 = Delta_l^2 / T_l^2 in Step 4 (+inf for T_l = 0
+< Delta_l, 0 for Delta_l = 0); ``VAR_PNORM`` takes the momentum scale |P|^2 =
+sum of P_l^2 over the momentum axes in place of P_l^2.
+
 Pure-Python loops: meant for cells of at most a few dozen particles.
 """
 from __future__ import annotations
@@ -20,6 +25,8 @@ from __future__ import annotations
 from fractions import Fraction
 
 INF = float("inf")
+VAR_NORMALIZED = 2
+VAR_PNORM = 4
 
 
 def _frac(x):
@@ -33,15 +40,27 @@ def _moments(q, w, members):
     return W, Q, var
 
 
-def _delta2(l, dx, var, Q, L):
-    """Delta_l squared (exact), +inf encoded as None."""
+def _delta2(l, dx, var, scale2, L):
+    """Delta_l squared (exact), +inf encoded as None; scale2 is the squared
+    momentum scale (P_l^2, or |P|^2)."""
     if l < dx:
         return var / (L[l] * L[l])
     if var == 0:
         return Fraction(0)
-    if Q == 0:
+    if scale2 == 0:
         return None
-    return var / (Q * Q)
+    return var / scale2
+
+
+def _score(d2, T2):
+    """(Delta / T)^2 for the normalised split axis; None is +inf."""
+    if d2 is None:
+        return None
+    if d2 == 0:
+        return Fraction(0)
+    if T2 == 0:
+        return None
+    return d2 / T2
 
 
 def _gt(a, b):
@@ -53,7 +72,7 @@ def _gt(a, b):
     return a > b
 
 
-def split_set(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1):
+def split_set(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1, variant=0):
     """Leaves of one set, each a list of member ids in input order, in
     V1-first depth-first order, with their exact centroids (W, X+P)."""
     dx, dp = len(pos), len(mom)
@@ -66,7 +85,9 @@ def split_set(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1):
 
     def rec(members):
         W, Q, var = _moments(q, wf, members)
-        d2 = [_delta2(l, dx, var[l], Q[l], L) for l in range(D)]
+        pn2 = sum(Q[l] * Q[l] for l in range(dx, D))
+        d2 = [_delta2(l, dx, var[l], pn2 if variant & VAR_PNORM else Q[l] * Q[l], L)
+              for l in range(D)]
         stop = all(d is not None and d <= T2[l] for l, d in enumerate(d2))
         if stop:
             if len(members) == 1:
@@ -75,9 +96,10 @@ def split_set(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1):
             else:
                 leaves.append((members, W, Q))
             return
+        key = [_score(d2[l], T2[l]) for l in range(D)] if variant & VAR_NORMALIZED else d2
         k = 0
         for l in range(1, D):
-            if _gt(d2[l], d2[k]):
+            if _gt(key[l], key[k]):
                 k = l
         v1 = [i for i in members if q[k][i] <= Q[k]]
         v2 = [i for i in members if q[k][i] > Q[k]]
@@ -90,7 +112,7 @@ def split_set(pos, mom, w, cell_size=(1.0, 1.0, 1.0), tol_x=0.1, tol_p=0.1):
 
 
 def merge(cell, pos, mom, w, n_cells, cell_size=(1.0, 1.0, 1.0), n_min=0,
-          tol_x=0.1, tol_p=0.1):
+          tol_x=0.1, tol_p=0.1, variant=0):
     """All cells: returns (index[n], centroids list of (cell, W, coords))
     with output slots in canonical order (cells ascending, leaves in
     V1-first depth-first order)."""
@@ -111,7 +133,8 @@ def merge(cell, pos, mom, w, n_cells, cell_size=(1.0, 1.0, 1.0), n_min=0,
         sub_pos = [[pos[l][i] for i in members] for l in range(len(pos))]
         sub_mom = [[mom[l][i] for i in members] for l in range(len(mom))]
         sub_w = [w[i] for i in members]
-        for local, W, coords in split_set(sub_pos, sub_mom, sub_w, cell_size, tol_x, tol_p):
+        for local, W, coords in split_set(sub_pos, sub_mom, sub_w, cell_size, tol_x, tol_p,
+                                          variant):
             for j in local:
                 index[members[j]] = len(out)
             out.append((c, W, coords))

@@ -30,6 +30,15 @@
  * Near-tie flags, recorded per cell (bit 0 stop test, bit 1 argmax, bit 2
  * cut): some |Delta_l - T_l| <= 1e-9 T_l; the top two Delta within 1e-9
  * relative; some |q_i - Q| <= 64 m eps (sum w|q|)/W on the cut axis.
+ *
+ * Two optional decision variants (bits of `variant`), off by default:
+ *   ORC_VAR_NORMALIZED  Step 4 takes the axis of the largest Delta_l / T_l
+ *                       (T_l = T_X or T_P; with T_l = 0 the ratio is +inf
+ *                       for Delta_l > 0 and 0 for Delta_l = 0).
+ *   ORC_VAR_PNORM       Delta_p uses the length of the mean momentum vector,
+ *                       Delta_l = sigma_l / |P| with |P| = sqrt(sum_l P_l^2)
+ *                       over the momentum axes, instead of |P_l|.
+ * The near-tie flags then refer to the values that the variant compares.
  */
 #include <float.h>
 #include <math.h>
@@ -50,12 +59,16 @@
 #define ORC_MAXD 6
 #define ORC_NEAR_REL 1e-9
 
+#define ORC_VAR_NORMALIZED 2u
+#define ORC_VAR_PNORM 4u
+
 typedef struct {
     int dx, dp, D;
     const double *q[ORC_MAXD]; /* q[l][i]: positions (l < dx) then momenta */
     const double *w;
     double L[3];
     double tol_x, tol_p;
+    unsigned variant;
 } orc_problem;
 
 typedef struct {
@@ -96,17 +109,28 @@ static void subset_moments(const orc_problem *P, const int64_t *idx, int64_t m,
             if (q[idx[i]] > qmax) qmax = q[idx[i]];
         }
         double sigma = (qmin == qmax) ? 0.0 : sqrt(v / W);
-        double delta;
+        M->Q[l] = Q;
+        M->sigma[l] = sigma;
+    }
+    /* the momentum scale of Eq. cv_p: |P_l|, or |P| for ORC_VAR_PNORM */
+    double pnorm = 0.0;
+    if (P->variant & ORC_VAR_PNORM) {
+        double s2 = 0.0;
+        for (int l = P->dx; l < P->D; ++l)
+            s2 += M->Q[l] * M->Q[l];
+        pnorm = sqrt(s2);
+    }
+    for (int l = 0; l < P->D; ++l) {
+        double sigma = M->sigma[l], delta;
+        double scale = (P->variant & ORC_VAR_PNORM) ? pnorm : fabs(M->Q[l]);
         if (l < P->dx)
             delta = sigma / P->L[l];
         else if (sigma == 0.0)
             delta = 0.0;
-        else if (Q == 0.0)
+        else if (scale == 0.0)
             delta = INFINITY;
         else
-            delta = sigma / fabs(Q);
-        M->Q[l] = Q;
-        M->sigma[l] = sigma;
+            delta = sigma / scale;
         M->delta[l] = delta;
     }
 }
@@ -125,17 +149,32 @@ static int stop_test(const orc_problem *P, const orc_moments *M, unsigned *near)
     return stop;
 }
 
+/* The value Step 4 maximises on axis l: Delta_l, or Delta_l / T_l. */
+static double axis_score(const orc_problem *P, const orc_moments *M, int l)
+{
+    double d = M->delta[l];
+    if (!(P->variant & ORC_VAR_NORMALIZED))
+        return d;
+    double T = (l < P->dx) ? P->tol_x : P->tol_p;
+    if (T == 0.0)
+        return d > 0.0 ? INFINITY : 0.0;
+    return d / T;
+}
+
 /* Step 4: axis of the largest CV. */
 static int split_axis(const orc_problem *P, const orc_moments *M, unsigned *near)
 {
+    double score[ORC_MAXD];
+    for (int l = 0; l < P->D; ++l)
+        score[l] = axis_score(P, M, l);
     int k = 0;
     for (int l = 1; l < P->D; ++l)
-        if (M->delta[l] > M->delta[k])
+        if (score[l] > score[k])
             k = l;
-    double top = M->delta[k];
+    double top = score[k];
     for (int l = 0; l < P->D; ++l) {
         if (l == k) continue;
-        double d = M->delta[l];
+        double d = score[l];
         if (isinf(top) ? isinf(d) : (d >= top * (1.0 - ORC_NEAR_REL)))
             *near |= ORC_NEAR_ARGMAX;
     }
@@ -264,10 +303,14 @@ static int64_t split_cell(const orc_problem *P, int64_t *idx, int64_t m,
 
 static int setup_problem(orc_problem *P, int dx, int dp, const double *pos,
                          const double *mom, int64_t stride, const double *w,
-                         const double *cell_size, double tol_x, double tol_p)
+                         const double *cell_size, double tol_x, double tol_p,
+                         unsigned variant)
 {
     if (dx < 1 || dx > 3 || dp < 1 || dp > 3)
         return ORC_ERR_ARG;
+    if (variant & ~(ORC_VAR_NORMALIZED | ORC_VAR_PNORM))
+        return ORC_ERR_ARG;
+    P->variant = variant;
     if (!(tol_x >= 0.0) || !(tol_p >= 0.0) || isinf(tol_x) || isinf(tol_p))
         return ORC_ERR_ARG;
     P->dx = dx;
@@ -294,10 +337,11 @@ static int setup_problem(orc_problem *P, int dx, int dp, const double *pos,
 int pma_oracle_subset_moments(int64_t m, int dx, int dp, const double *pos,
                               const double *mom, int64_t stride, const double *w,
                               const int64_t *idx, const double *cell_size,
-                              double *W, double *Q, double *sigma, double *delta)
+                              double *W, double *Q, double *sigma, double *delta,
+                              unsigned variant)
 {
     orc_problem P;
-    int rc = setup_problem(&P, dx, dp, pos, mom, stride, w, cell_size, 0.0, 0.0);
+    int rc = setup_problem(&P, dx, dp, pos, mom, stride, w, cell_size, 0.0, 0.0, variant);
     if (rc) return rc;
     if (m < 1) return ORC_ERR_ARG;
     int64_t *all = NULL;
@@ -328,10 +372,10 @@ int pma_oracle_trace(int64_t m, int dx, int dp, const double *pos,
                      double tol_x, double tol_p, int64_t *perm,
                      int64_t *node_begin, int64_t *node_end, int64_t *node_depth,
                      int32_t *node_axis, double *node_Q, int64_t *n_nodes,
-                     uint32_t *near)
+                     uint32_t *near, unsigned variant)
 {
     orc_problem P;
-    int rc = setup_problem(&P, dx, dp, pos, mom, m, w, cell_size, tol_x, tol_p);
+    int rc = setup_problem(&P, dx, dp, pos, mom, m, w, cell_size, tol_x, tol_p, variant);
     if (rc) return rc;
     if (m < 1) return ORC_ERR_ARG;
     orc_scratch S;
@@ -454,12 +498,12 @@ int pma_oracle_merge(int64_t n, const int32_t *cell, int dx, int dp,
                      double tol_x, double tol_p, int n_threads,
                      int32_t *out_cell, double *out_pos, double *out_mom,
                      double *out_w, int32_t *out_index, uint8_t *cell_flags,
-                     int64_t *out_count, orc_stats *stats)
+                     int64_t *out_count, orc_stats *stats, unsigned variant)
 {
     if (n < 0 || n_cells < 1 || n_min < 0 || !out_count)
         return ORC_ERR_ARG;
     orc_problem P;
-    int rc = setup_problem(&P, dx, dp, pos, mom, n, w, cell_size, tol_x, tol_p);
+    int rc = setup_problem(&P, dx, dp, pos, mom, n, w, cell_size, tol_x, tol_p, variant);
     if (rc) return rc;
     for (int64_t i = 0; i < n; ++i) {
         if (cell[i] < 0 || (int64_t)cell[i] >= n_cells) return ORC_ERR_INPUT;

@@ -67,6 +67,26 @@ def pin_failures(lib):
     ok = abs(r.w.sum() - p.w.sum()) < 1e-9 and all(
         abs(np.sum(r.w * r.mom[l]) - np.sum(p.w * p.mom[l])) < 1e-9 for l in range(3))
     check("conservation", ok)
+    # momentum-norm variant: p = (0.6, 0.7, 0), (0.6, 0.9, 0); mean (0.6, 0.8, 0),
+    # |P| = 1, sigma_y = 0.1, so Delta_y = 0.1 (the literal rule: 0.1/0.8)
+    pos = np.full((1, 2), 0.5)
+    mom = np.array([[0.6, 0.6], [0.7, 0.9], [0.0, 0.0]])
+    r = oracle.merge(z2, pos, mom, np.ones(2), 1, tol_x=1.0, tol_p=0.11, lib=lib,
+                     variant=oracle.VAR_PNORM)
+    check("pnorm_merge", r.count == 1)
+    r = oracle.merge(z2, pos, mom, np.ones(2), 1, tol_x=1.0, tol_p=0.09, lib=lib,
+                     variant=oracle.VAR_PNORM)
+    check("pnorm_split", r.count == 2)
+    # normalised split axis: Delta_x = 0.3, Delta_p = 0.5; with T_X = 0.1 and
+    # T_P = 0.25 the ratios are 3 and 2, so x is cut (the literal rule cuts p)
+    xs, ps = np.array([[0.2, 0.8, 0.2, 0.8]]), np.array([[1.0, 1.0, 3.0, 3.0]])
+    t = oracle.trace(xs, ps, np.ones(4), tol_x=0.1, tol_p=0.25, lib=lib,
+                     variant=oracle.VAR_NORMALIZED)
+    check("normalized_axis", t.axis[0] == 0)
+    # T_X = 0: any position spread is an infinite ratio
+    t = oracle.trace(xs, ps, np.ones(4), tol_x=0.0, tol_p=1.0, lib=lib,
+                     variant=oracle.VAR_NORMALIZED)
+    check("normalized_zero_tol", t.axis[0] == 0)
     return fails
 
 
@@ -75,17 +95,22 @@ def test_real_oracle_passes_compact_pins():
 
 
 MUTANTS = {
-    "drop_abs_of_mean": ("delta = sigma / fabs(Q);", "delta = sigma / Q;"),
+    "drop_abs_of_mean": ("fabs(M->Q[l])", "M->Q[l]"),
     "bessel_variance": ("sqrt(v / W)", "sqrt(v / (W - 1.0))"),
     "unweighted_mean": ("s += P->w[idx[i]] * q[idx[i]];", "s += q[idx[i]];"),
     "stop_strict": ("if (!(M->delta[l] <= T))", "if (!(M->delta[l] < T))"),
-    "argmin": ("if (M->delta[l] > M->delta[k])", "if (M->delta[l] < M->delta[k])"),
+    "argmin": ("if (score[l] > score[k])", "if (score[l] < score[k])"),
     "cut_strict": ("q[sub[i]] <= Qk", "q[sub[i]] < Qk"),
     "v2_first": ("        S->stack[sp++] = (orc_range){r.begin + n1, r.end, r.depth + 1};\n"
                  "        S->stack[sp++] = (orc_range){r.begin, r.begin + n1, r.depth + 1};",
                  "        S->stack[sp++] = (orc_range){r.begin, r.begin + n1, r.depth + 1};\n"
                  "        S->stack[sp++] = (orc_range){r.begin + n1, r.end, r.depth + 1};"),
     "leaf_weight_count": ("L->W = M.W;", "L->W = (double)ms;"),
+    "pnorm_sum_abs": ("s2 += M->Q[l] * M->Q[l];", "s2 += fabs(M->Q[l]);"),
+    "pnorm_ignored": ("double scale = (P->variant & ORC_VAR_PNORM) ? pnorm : fabs(M->Q[l]);",
+                      "double scale = fabs(M->Q[l]);"),
+    "normalized_ignores_T": ("return d / T;", "return d;"),
+    "normalized_zero_tol": ("return d > 0.0 ? INFINITY : 0.0;", "return 0.0;"),
 }
 
 

@@ -1,0 +1,176 @@
+"""Pins of the oracle's two optional decision variants, against facts fixed
+outside the oracle.
+
+* ``VAR_NORMALIZED``: Step 4 takes the axis of the largest Delta_l / T_l
+  instead of the largest raw Delta_l.
+* ``VAR_PNORM``: the momentum CV of Eq. cv_p divides sigma_l by |P|, the
+  length of the mean momentum vector, instead of |P_l|.
+
+Pins: exact rational arithmetic, reductions to the literal rule where the
+variant cannot change anything (one momentum axis; equal tolerances), numpy
+statistics at every node of the tree, and a symmetry (relabelling the
+momentum axes leaves the partition unchanged under ``VAR_PNORM``).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from paper_1504_00636_gb300 import synth
+
+VARIANTS = [oracle.VAR_NORMALIZED, oracle.VAR_PNORM,
+            oracle.VAR_NORMALIZED | oracle.VAR_PNORM]
+IDS = ["normalized", "pnorm", "both"]
+
+
+def np_stats_variant(pos, mom, w, variant, L=(1.0, 1.0, 1.0)):
+    """Delta of one set via numpy's weighted average / covariance."""
+    q = np.concatenate([np.atleast_2d(pos), np.atleast_2d(mom)])
+    dx = np.atleast_2d(pos).shape[0]
+    Q = np.average(q, axis=1, weights=w)
+    sig = np.array([math.sqrt(max(0.0, float(np.cov(q[l], aweights=w, bias=True))))
+                    if q.shape[1] > 1 else 0.0 for l in range(q.shape[0])])
+    pn = float(np.linalg.norm(Q[dx:]))
+    delta = np.empty_like(sig)
+    for l in range(q.shape[0]):
+        scale = pn if variant & oracle.VAR_PNORM else abs(Q[l])
+        if l < dx:
+            delta[l] = sig[l] / L[l]
+        elif sig[l] == 0.0:
+            delta[l] = 0.0
+        elif scale == 0.0:
+            delta[l] = math.inf
+        else:
+            delta[l] = sig[l] / scale
+    return Q, delta
+
+
+def _partition(r, n):
+    groups = {}
+    for i in range(n):
+        groups.setdefault(int(r.index[i]), []).append(i)
+    return sorted(tuple(g) for g in groups.values())
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("seed", range(6))
+def test_variant_equals_exact_rational(variant, seed):
+    rng = np.random.default_rng(500 + seed)
+    dx = 1 + seed % 3
+    p = synth.random_cell(rng, 10 + 4 * seed, dx, 3, drift=(0.25, -0.05, 0.02),
+                          spread=0.08, weights="lognormal" if seed % 2 else "uniform")
+    tx, tp = 0.25, 0.12
+    r = oracle.merge_particles(p, tol_x=tx, tol_p=tp, variant=variant)
+    idx, out = exact.merge(p.cell, p.pos, p.mom, p.w, 1, tol_x=tx, tol_p=tp,
+                           variant=variant)
+    if r.flags[0]:
+        pytest.skip("near tie")
+    assert r.count == len(out)
+    assert list(r.index) == idx
+    for j, (c, W, coords) in enumerate(out):
+        assert r.w[j] == pytest.approx(float(W), rel=1e-14)
+        got = np.concatenate([r.pos[:, j], r.mom[:, j]])
+        np.testing.assert_allclose(got, [float(x) for x in coords], rtol=1e-13, atol=1e-15)
+
+
+def test_variants_change_decisions_on_these_sets():
+    # the exact-rational sets above are not all decided alike by the literal
+    # rule and the variants (otherwise the agreement would pin nothing new)
+    differs = {v: 0 for v in VARIANTS}
+    for seed in range(6):
+        rng = np.random.default_rng(500 + seed)
+        p = synth.random_cell(rng, 10 + 4 * seed, 1 + seed % 3, 3,
+                              drift=(0.25, -0.05, 0.02), spread=0.08,
+                              weights="lognormal" if seed % 2 else "uniform")
+        base = oracle.merge_particles(p, tol_x=0.25, tol_p=0.12)
+        for v in VARIANTS:
+            r = oracle.merge_particles(p, tol_x=0.25, tol_p=0.12, variant=v)
+            differs[v] += list(r.index) != list(base.index)
+    assert all(n > 0 for n in differs.values()), differs
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pnorm_with_one_momentum_axis_is_the_literal_rule(seed):
+    # dp = 1: |P| = |P_x|
+    rng = np.random.default_rng(600 + seed)
+    p = synth.random_cell(rng, 300, 2, 1, drift=(0.3,), spread=0.1, weights="lognormal")
+    a = oracle.merge_particles(p, tol_x=0.2, tol_p=0.1)
+    b = oracle.merge_particles(p, tol_x=0.2, tol_p=0.1, variant=oracle.VAR_PNORM)
+    np.testing.assert_array_equal(a.index, b.index)
+    np.testing.assert_array_equal(a.mom, b.mom)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_normalized_with_equal_tolerances_is_the_literal_rule(seed):
+    # T_X = T_P: Delta_l / T orders the axes as Delta_l does
+    rng = np.random.default_rng(700 + seed)
+    p = synth.random_cell(rng, 400, 1 + seed, 3, drift=(0.3, 0.1, -0.2), spread=0.1)
+    for v in (0, oracle.VAR_PNORM):
+        a = oracle.merge_particles(p, tol_x=0.15, tol_p=0.15, variant=v)
+        b = oracle.merge_particles(p, tol_x=0.15, tol_p=0.15,
+                                   variant=v | oracle.VAR_NORMALIZED)
+        np.testing.assert_array_equal(a.index, b.index)
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("seed", range(3))
+def test_variant_tree_invariants(variant, seed):
+    # at every node, recomputed with numpy: a leaf passes the stop test, an
+    # inner node fails it and is cut on the axis the variant maximises
+    rng = np.random.default_rng(800 + seed)
+    dx = 1 + seed
+    p = synth.random_cell(rng, 120, dx, 3, drift=(0.3, 0.0, 0.05), spread=0.06,
+                          weights="lognormal")
+    tx, tp = 0.3, 0.1
+    t = oracle.trace(p.pos, p.mom, p.w, tol_x=tx, tol_p=tp, variant=variant)
+    tol = np.array([tx] * dx + [tp] * 3)
+    for j in range(len(t.begin)):
+        mem = t.perm[t.begin[j]:t.end[j]]
+        Q, dl = np_stats_variant(p.pos[:, mem], p.mom[:, mem], p.w[mem], variant)
+        ok = bool(np.all(dl <= tol))
+        if t.axis[j] < 0:
+            assert ok or t.near
+            continue
+        assert not ok or t.near
+        score = dl / tol if variant & oracle.VAR_NORMALIZED else dl
+        k = t.axis[j]
+        assert score[k] == pytest.approx(np.max(score), rel=1e-9) or t.near
+        assert t.Q[j] == pytest.approx(Q[k], rel=1e-12, abs=1e-15)
+
+
+@pytest.mark.parametrize("perm", [(1, 0, 2), (2, 1, 0), (1, 2, 0)])
+def test_pnorm_partition_ignores_momentum_axis_labels(perm):
+    # |P| and the set {sigma_l} do not depend on how the momentum axes are
+    # labelled, so neither does the partition (no exact ties on this data)
+    p = synth.counter_beams(cells=3)
+    q = dataclass_replace_mom(p, p.mom[list(perm)])
+    a = oracle.merge_particles(p, variant=oracle.VAR_PNORM)
+    b = oracle.merge_particles(q, variant=oracle.VAR_PNORM)
+    assert not a.flags.any() and not b.flags.any()
+    assert _partition(a, p.n) == _partition(b, p.n)
+
+
+def dataclass_replace_mom(p, mom):
+    import dataclasses
+    return dataclasses.replace(p, mom=np.ascontiguousarray(mom))
+
+
+def test_pnorm_cuts_fragmentation_on_transverse_axes():
+    # counter-streaming beams with thermal transverse spread around p_y = p_z
+    # = 0: the literal |P_l| makes those axes split down to single particles
+    # (near zero mean), |P| does not
+    p = synth.counter_beams(cells=4)
+    lit = oracle.merge_particles(p)
+    pn = oracle.merge_particles(p, variant=oracle.VAR_PNORM)
+    assert pn.count < lit.count / 4
+    assert pn.stats["depth_sum"] < lit.stats["depth_sum"]
+
+
+def test_unknown_variant_bits_are_rejected():
+    p = synth.counter_beams(cells=1)
+    with pytest.raises(ValueError):
+        oracle.merge_particles(p, variant=1)
+    with pytest.raises(ValueError):
+        oracle.merge_particles(p, variant=8)
