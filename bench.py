@@ -145,7 +145,7 @@ def bytes_per_particle(p, mixed):
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("warp.cu", "split_common.cuh", "pma_device.cuh"):
+    for f in ("team.cuh", "warp.cu", "split_common.cuh", "pma_device.cuh"):
         with open(os.path.join(ROOT, "paper_1504_00636_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

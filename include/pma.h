@@ -54,6 +54,20 @@ extern "C" {
 
 /* ---- config flags ---------------------------------------------------- */
 #define PMA_FLAG_NO_INDEX 1u  /* do not accept an output index (saves 4 B/particle) */
+/*
+ * Decision variants.  Off by default: the default is the paper's rule as
+ * printed (Step 4 takes the largest raw Delta_l; Eq. cv_p divides by |P_l|).
+ *   PMA_FLAG_SPLIT_NORMALIZED  Step 4 takes the axis of the largest
+ *       Delta_l / T_l (T_l = T_X on position axes, T_P on momentum axes; with
+ *       T_l = 0 the ratio is +inf when Delta_l > 0 and 0 when Delta_l = 0).
+ *   PMA_FLAG_MOMENTUM_NORM  Eq. cv_p uses the length of the mean momentum
+ *       vector: Delta_l = sigma_l / |P|, |P| = sqrt(sum over momentum axes
+ *       of P_l^2), instead of sigma_l / |P_l|.  Sets whose mean momentum is
+ *       near zero on one axis then stop splitting on that axis.
+ * Both apply to pma_merge and pma_merge_host; pma_merge_noalloc ignores them.
+ */
+#define PMA_FLAG_SPLIT_NORMALIZED 2u
+#define PMA_FLAG_MOMENTUM_NORM 4u
 
 typedef struct pma_handle pma_handle;
 

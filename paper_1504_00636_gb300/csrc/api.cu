@@ -196,6 +196,8 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   if (cfg->n_min < 0) return PMA_ERR_INVALID_ARG;
   if (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED) return PMA_ERR_INVALID_ARG;
   if (cfg->capacity < 0 || cfg->capacity > INT32_MAX) return PMA_ERR_INVALID_ARG;
+  if (cfg->flags & ~(PMA_FLAG_NO_INDEX | PMA_FLAG_SPLIT_NORMALIZED | PMA_FLAG_MOMENTUM_NORM))
+    return PMA_ERR_INVALID_ARG;
   for (int a = 0; a < cfg->dx; ++a)
     if (!(cfg->cell_size[a] > 0.0) || !std::isfinite(cfg->cell_size[a]))
       return PMA_ERR_INVALID_ARG;
@@ -346,6 +348,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.dx = h->cfg.dx;
   P.D = h->D;
   P.n_min = h->cfg.n_min;
+  P.variant = ((h->cfg.flags & PMA_FLAG_SPLIT_NORMALIZED) ? kVarNormalized : 0) |
+              ((h->cfg.flags & PMA_FLAG_MOMENTUM_NORM) ? kVarPNorm : 0);
   P.cap = h->cap;
   P.unsorted = &h->ctl->unsorted;
   P.tol2_x = tol_x * tol_x;

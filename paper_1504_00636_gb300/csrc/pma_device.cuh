@@ -49,11 +49,16 @@ __host__ __device__ __forceinline__ uint8_t head_code(int m) {
   return (uint8_t)(m < 255 ? m : 255);
 }
 
+// decision variants (Problem::variant bits)
+constexpr int kVarNormalized = 2;  // Step 4 on Delta_l / T_l
+constexpr int kVarPNorm = 4;       // Eq. cv_p with |P| of the mean momentum vector
+
 struct Problem {
   int32_t n_cells;
   int32_t dx;
   int32_t D;
   int32_t n_min;
+  int32_t variant;      // kVarNormalized | kVarPNorm, or 0 for the literal rule
   int32_t cap;          // particles per unit held in shared memory
   const int32_t *unsorted;  // device flag: 0 when cell ids are non-decreasing
   double tol2_x, tol2_p;  // T^2
@@ -204,14 +209,26 @@ struct Cut {
 };
 
 // Steps 3-5 in FP64 from moment values (W, m1, m2 about the shift s).
-template <int D>
+// VAR = false: the paper's rule only; true: the variants in P.variant.
+template <int D, bool VAR = true>
 __device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const double *m1,
                                            const double *m2, const double *s) {
   Cut c;
   c.leaf = 1;
   c.k = 0;
+  const bool normd = VAR && (P.variant & kVarNormalized) != 0;
+  const bool pnorm = VAR && (P.variant & kVarPNorm) != 0;
   double bestV = -1.0, bestDen = 1.0;
   double W2 = W * W;
+  double denN = 0.0;  // (W |P|)^2 for the momentum-norm variant
+  if (pnorm) {
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l >= P.dx) {
+        const double Pw = fma(s[l], W, m1[l]);
+        denN = fma(Pw, Pw, denN);
+      }
+  }
 #pragma unroll
   for (int l = 0; l < D; ++l) {
     double V = fmax(fma(m2[l], W, -m1[l] * m1[l]), 0.0);
@@ -221,15 +238,18 @@ __device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const dou
       tol2 = P.tol2_x;
     } else {
       double Pw = fma(s[l], W, m1[l]);
-      den = Pw * Pw;
+      den = pnorm ? denN : Pw * Pw;
       tol2 = P.tol2_p;
     }
     // Delta_l <= T  <=>  V <= T^2 den  (den = 0: only V = 0 passes)
     if (!(V <= tol2 * den)) c.leaf = 0;
-    // first maximum of Delta_l = sqrt(V / den)
-    if (bestV < 0.0 || V * bestDen > bestV * den) {
+    // first maximum of V / kden = Delta_l^2, or (Delta_l / T_l)^2 for the
+    // normalised variant; kden = 0 is +infinity, and V = 0 counts as 0
+    double kden = normd ? den * tol2 : den;
+    if (V == 0.0) kden = 1.0;
+    if (bestV < 0.0 || V * bestDen > bestV * kden) {
       bestV = V;
-      bestDen = den;
+      bestDen = kden;
       c.k = l;
     }
   }
@@ -246,7 +266,7 @@ __device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const dou
 // are evaluated in FP32 with an error bound; when a comparison is closer
 // than the bound the FP64 evaluation of the same sums decides.  The cut value
 // is computed as a double-float (hi + lo) and rounded down to float.
-template <int D>
+template <int D, bool VAR = true>
 __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<float, D> &M,
                                             const float *s) {
   const float g = 1.0f / (1 << 17);  // error budget relative to the terms
@@ -256,8 +276,25 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   c.leaf = 1;
   c.k = 0;
   bool sure = true;
-  // first and second largest Delta^2 (position: V / (L W)^2, momentum:
-  // V / (W P)^2; den = 0 is +infinity unless V = 0)
+  const bool normd = VAR && (P.variant & kVarNormalized) != 0;
+  const bool pnorm = VAR && (P.variant & kVarPNorm) != 0;
+  // momentum-norm variant: (W |P|)^2 and its error bound
+  float denN = 0.f, eDN = 0.f;
+  if (pnorm) {
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l >= P.dx) {
+        const float m1 = M.m1[l].hi();
+        const float Pw = fmaf(s[l], W, m1);
+        const float eP = g * (fabsf(s[l] * W) + fabsf(m1));
+        denN = fmaf(Pw, Pw, denN);
+        eDN += 2.f * fabsf(Pw) * eP + eP * eP;
+      }
+    eDN += g * denN;
+  }
+  // first and second largest V / kden: Delta^2 (position: V / (L W)^2,
+  // momentum: V / (W P)^2), or (Delta / T)^2 for the normalised variant;
+  // kden = 0 is +infinity unless V = 0
   float r1 = -1.f, r2 = -1.f;
 #pragma unroll
   for (int l = 0; l < D; ++l) {
@@ -270,6 +307,10 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
       den = P.L2f[l] * W2;
       eD = g * den;
       tol2 = P.tol2_xf;
+    } else if (pnorm) {
+      den = denN;
+      eD = eDN;
+      tol2 = P.tol2_pf;
     } else {
       float Pw = fmaf(s[l], W, m1);
       float eP = g * (fabsf(s[l] * W) + fabsf(m1));
@@ -280,14 +321,15 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
     float f = V - tol2 * den;
     if (fabsf(f) <= eV + tol2 * eD) sure = false;
     if (f > 0.f) c.leaf = 0;
+    const float kden = normd ? den * tol2 : den, eK = normd ? eD * tol2 : eD;
     float r;
     if (V == 0.f)
       r = 0.f;
-    else if (den <= eD)
+    else if (kden <= eK)
       r = __int_as_float(0x7f800000);
     else
-      r = __fdividef(V, den);
-    if (V != 0.f && (V <= eV || den <= eD)) sure = false;
+      r = __fdividef(V, kden);
+    if (V != 0.f && (V <= eV || kden <= eK)) sure = false;
     if (r > r1) {
       r2 = r1;
       r1 = r;
@@ -306,7 +348,7 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
       m2d[l] = M.m2[l].value();
       sd[l] = (double)s[l];
     }
-    Cut d = decide_fp64<D>(P, W64, m1d, m2d, sd);
+    Cut d = decide_fp64<D, VAR>(P, W64, m1d, m2d, sd);
     d.Q = 0.0;
     c.leaf = d.leaf;
     c.k = d.k;

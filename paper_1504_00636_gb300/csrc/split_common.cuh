@@ -30,11 +30,12 @@ __device__ __forceinline__ bool finite_val(T x) {
 
 // ------------------------------------------------------------ cut helpers
 
-template <typename T, int D>
+// VAR = false compiles the paper's rule only; true reads Problem::variant
+template <typename T, int D, bool VAR = true>
 struct Decider;
 
-template <int D>
-struct Decider<double, D> {
+template <int D, bool VAR>
+struct Decider<double, D, VAR> {
   __device__ static __forceinline__ Cut run(const Problem &P, const Moments<double, D> &M,
                                             const double *s) {
     double m1[D], m2[D];
@@ -43,16 +44,16 @@ struct Decider<double, D> {
       m1[l] = M.m1[l].v;
       m2[l] = M.m2[l].v;
     }
-    return decide_fp64<D>(P, M.W.v, m1, m2, s);
+    return decide_fp64<D, VAR>(P, M.W.v, m1, m2, s);
   }
   __device__ static __forceinline__ bool left(double q, const Cut &c) { return q <= c.Q; }
 };
 
-template <int D>
-struct Decider<float, D> {
+template <int D, bool VAR>
+struct Decider<float, D, VAR> {
   __device__ static __forceinline__ Cut run(const Problem &P, const Moments<float, D> &M,
                                             const float *s) {
-    return decide_mixed<D>(P, M, s);
+    return decide_mixed<D, VAR>(P, M, s);
   }
   __device__ static __forceinline__ bool left(float q, const Cut &c) { return q <= c.Qt; }
 };

@@ -1,0 +1,554 @@
+// Team kernel: Sec. 3, Steps 2-6 for every unit that fits one CTA's shared
+// memory (a cell, or a piece of a cell first cut in global memory), and the
+// verbatim copy of cells with N <= N_min.
+//
+// A team of 4 or 8 warps owns one unit at a time.  The unit's coordinates and
+// weights are staged once in shared memory (SoA columns) and stay in place.
+// A subset is a contiguous range of a 16-bit index array; a cut writes
+// V1 = {q_k <= Q_k} to the front and V2 to the back of the same range in the
+// other index array (double-buffered by tree depth), so the final sets come
+// out in V1-first depth-first order when listed by position, whatever order
+// the subsets are processed in.
+//
+// Pending subsets wait on one stack per size class.  A round takes up to
+// 32/G subsets of one class per warp and gives each a group of G lanes
+// (G = 32 for the largest sets down to G = 1, so that a lane reads a dozen
+// particles or so): moments by lane-strided sums and a butterfly inside the
+// group, Steps 3-5, and the cut by group-masked ballots.  Two-particle sets
+// have their own round, the same arithmetic without loops.  CTA barriers
+// separate rounds.
+//
+// The template flag VAR selects the decision: false compiles the paper's rule
+// only; true reads the optional variants (normalised split axis, momentum
+// norm) from the problem at run time.  The two builds live in separate
+// translation units (warp.cu, warp_var.cu).
+#pragma once
+
+#include "pma_device.cuh"
+#include "pma_launch.h"
+#include "split_common.cuh"
+
+namespace pma {
+
+constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
+constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
+constexpr int kMaxCapW = 8191;
+
+// size class of a subset of m >= 2 particles
+__device__ __forceinline__ int size_class(int m) {
+  if (m == 2) return 0;
+  if (m <= 12) return 1;
+  if (m <= 24) return 2;
+  if (m <= 48) return 3;
+  if (m <= 96) return 4;
+  if (m <= 192) return 5;
+  return 6;
+}
+
+// most subsets of a class that can be pending at once: they are disjoint
+// subsets of at least lo particles of one tile of at most cap
+__host__ __device__ inline int class_capacity(int c, int cap) {
+  // smallest size of class c: 2, 3, 13, 25, 49, 97, 193
+  const int lo = c == 0 ? 2 : (c == 1 ? 3 : (12 << (c - 2)) + 1);
+  return cap / lo;
+}
+
+__host__ __device__ inline int stacks_entries(int cap) {
+  int t = 0;
+  for (int c = 0; c < kClasses; ++c) t += class_capacity(c, cap);
+  return t;
+}
+
+// subset record: begin (13 bits) | length (13 bits) << 13 | parity << 26
+__device__ __forceinline__ uint32_t pack_rec(int b, int m, int par) {
+  return (uint32_t)b | ((uint32_t)m << 13) | ((uint32_t)par << 26);
+}
+__device__ __forceinline__ int rec_begin(uint32_t r) { return (int)(r & 8191u); }
+__device__ __forceinline__ int rec_len(uint32_t r) { return (int)((r >> 13) & 8191u); }
+__device__ __forceinline__ int rec_par(uint32_t r) { return (int)((r >> 26) & 1u); }
+
+// Views into the tile's shared memory.  Every member is a plain pointer or
+// integer (no arrays), so the struct lives in registers.
+template <typename T, int D>
+struct WarpTile {
+  T *data;         // [D + 1][cap]: coordinates, then weight
+  uint16_t *idx0;  // [2][cap] index arrays, by depth parity
+  uint32_t *stk0;  // the class stacks, back to back
+  int *top;        // [kClasses] stack heights
+  uint16_t *soff;  // [kClasses] first entry of each stack, [kClasses] capacities
+  int cap;
+  __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
+  __device__ __forceinline__ uint16_t *idx(int par) const { return idx0 + par * cap; }
+  __device__ __forceinline__ uint32_t *stk(int c) const { return stk0 + soff[c]; }
+  __device__ __forceinline__ int stk_cap(int c) const { return soff[kClasses + c]; }
+};
+
+template <typename T, int D>
+__host__ __device__ inline size_t warp_region_bytes(int cap) {
+  size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
+  b = (b + 15) & ~size_t(15);
+  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 1) * sizeof(int) +
+       2 * kClasses * sizeof(uint16_t);
+  return (b + 15) & ~size_t(15);
+}
+
+struct Counters {
+  unsigned long long leaves, depth, splits, degenerate;
+};
+
+// particle j of the tile, staged at final position gp
+template <typename T, int D>
+__device__ __forceinline__ void stage(const Problem &P, const WarpTile<T, D> &S, int64_t gp,
+                                      int j) {
+#pragma unroll
+  for (int l = 0; l <= D; ++l) static_cast<T *>(P.fin[l])[gp] = S.col(l)[j];
+}
+
+// A final set's positions [b, b + m) belong to no other subset, so both
+// index buffers are free there: buffer 0 takes the tile index of the particle
+// at each final position and buffer 1 its head code (Step 7 input); the unit
+// is written out to global memory in one coalesced pass at its end.
+template <typename T, int D>
+__device__ __forceinline__ void mark_final(const WarpTile<T, D> &S, int pos, int j, int h) {
+  S.idx(0)[pos] = (uint16_t)j;
+  S.idx(1)[pos] = (uint16_t)h;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void emit_single(const Problem &, const WarpTile<T, D> &S,
+                                            const int32_t *, int64_t, int pos, int j) {
+  mark_final<T, D>(S, pos, j, kHeadSingle);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D> &S,
+                                           const int32_t *perm, int64_t gb, int b, int m,
+                                           int par, Counters &cnt) {
+  if (m == 1) {
+    emit_single<T, D>(P, S, perm, gb, b, S.idx(par)[b]);
+    cnt.leaves += 1;
+    return;
+  }
+  const int c = size_class(m);
+  const int slot = atomicAdd(&S.top[c], 1);
+  if (slot < S.stk_cap(c))
+    S.stk(c)[slot] = pack_rec(b, m, par);
+  else
+    set_error(P.err, kErrInternal);
+}
+
+// one round of class c >= 1 for this warp: kw <= 32/G subsets (stack
+// entries base, base - 1, ...), G lanes each
+template <typename T, int D, bool VAR>
+__device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                            int64_t gb, int c, int lane, Counters &cnt, int kw, int base) {
+  const int lg = c - 1, G = 1 << lg;
+  const int gid = lane >> lg, gl = lane & (G - 1);
+  const bool act = gid < kw;
+  const uint32_t rec = act ? S.stk(c)[base - gid] : 0u;
+  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
+
+  // Steps 1-2: moments about the set's first particle
+  T s[D];
+  {
+    const int j0 = act ? S.idx(par)[b] : 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
+  }
+  Moments<T, D> M;
+  M.zero();
+#pragma unroll 4
+  for (int i = gl; i < m; i += G) {
+    const int j = S.idx(par)[b + i];
+    T q[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+    M.add(S.col(D)[j], q, s);
+  }
+  __syncwarp();
+  M.group_allreduce(G);
+  // Steps 3-5
+  Cut cut;
+  cut.leaf = 1;
+  cut.k = 0;
+  cut.Q = 0.0;
+  cut.Qt = 0.f;
+  if (act) cut = Decider<T, D, VAR>::run(P, M, s);
+  const bool split = act && !cut.leaf;
+  // Step 6: cut by group-masked ballot scan into the other index buffer
+  const int np = par ^ 1;
+  const T *qk = S.col(cut.k);
+  int cntL = 0, cntR = 0;
+  if (G == 1) {
+    // one lane per set: a serial stable-front / reversed-back partition
+    if (split)
+#pragma unroll 4
+      for (int i = 0; i < m; ++i) {
+        const int j = S.idx(par)[b + i];
+        const int dst = Decider<T, D, VAR>::left(qk[j], cut) ? (b + cntL++) : (b + m - 1 - cntR++);
+        S.idx(np)[dst] = (uint16_t)j;
+      }
+  } else {
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
+    const unsigned lt = lanemask_lt();
+    const int mmax = __reduce_max_sync(0xffffffffu, split ? (unsigned)m : 0u);
+    for (int base = 0; base < mmax; base += G) {
+      const int i = base + gl;
+      const bool valid = split && i < m;
+      const int j = valid ? S.idx(par)[b + i] : 0;
+      const bool lft = valid && Decider<T, D, VAR>::left(qk[j], cut);
+      const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
+      const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
+      if (valid) {
+        const int dst =
+            lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
+        S.idx(np)[dst] = (uint16_t)j;
+      }
+      cntL += __popc(bl);
+      cntR += __popc(br);
+    }
+  }
+  __syncwarp();
+  const bool degenerate = split && (cntL == 0 || cntR == 0);
+  const bool final_set = act && (cut.leaf || degenerate);
+  const int epar = cut.leaf ? par : np;
+  // final sets: final order and head codes (Step 7 sums them up later)
+  if (final_set) {
+    const int h = head_code(m);
+    for (int i = gl; i < m; i += G)
+      mark_final<T, D>(S, b + i, S.idx(epar)[b + i], i == 0 ? h : 0);
+  }
+  if (gl == 0 && act) {
+    if (final_set) {
+      cnt.leaves += 1;
+      if (degenerate) cnt.degenerate += 1;
+    } else {
+      cnt.splits += 1;
+      cnt.depth += (unsigned long long)m;
+      push_child<T, D>(P, S, perm, gb, b, cntL, np, cnt);
+      push_child<T, D>(P, S, perm, gb, b + cntL, m - cntL, np, cnt);
+    }
+  }
+  __syncwarp();
+}
+
+// one round of two-particle sets for this warp: kw <= 32 of them (stack
+// entries base, base - 1, ...), one per lane
+template <typename T, int D, bool VAR>
+__device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                           int64_t gb, int lane, Counters &cnt, int kw, int base) {
+  const bool act = lane < kw;
+  const uint32_t rec = act ? S.stk(0)[base - lane] : 0u;
+  if (!act) return;
+  const int b = rec_begin(rec), par = rec_par(rec);
+  const int ja = S.idx(par)[b], jb = S.idx(par)[b + 1];
+  T qa[D], qb[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    qa[l] = S.col(l)[ja];
+    qb[l] = S.col(l)[jb];
+  }
+  const T wa = S.col(D)[ja], wb = S.col(D)[jb];
+  // the same sums as the general path takes for two particles
+  Moments<T, D> M;
+  M.zero();
+  M.add(wa, qa, qa);
+  M.add(wb, qb, qa);
+  const Cut cut = Decider<T, D, VAR>::run(P, M, qa);
+  bool merged = cut.leaf != 0;
+  int first = ja, second = jb;
+  if (!merged) {
+    T ka = qa[0], kb = qb[0];
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l == cut.k) {
+        ka = qa[l];
+        kb = qb[l];
+      }
+    const bool la = Decider<T, D, VAR>::left(ka, cut), lb = Decider<T, D, VAR>::left(kb, cut);
+    if (la == lb) {
+      merged = true;  // degenerate cut: the set stays whole
+      cnt.degenerate += 1;
+    } else if (!la) {
+      first = jb;
+      second = ja;
+    }
+  }
+  if (merged) {
+    mark_final<T, D>(S, b, first, kHeadMerged);
+    mark_final<T, D>(S, b + 1, second, 0);
+    cnt.leaves += 1;
+  } else {
+    mark_final<T, D>(S, b, first, kHeadSingle);
+    mark_final<T, D>(S, b + 1, second, kHeadSingle);
+    cnt.leaves += 2;
+    cnt.splits += 1;
+    cnt.depth += 2;
+  }
+}
+
+// --------------------------------------------------------------- kernel
+
+// Work sources: mode 0 the cells of the small class (and pass-through
+// cells), mode 1 the cells of the large class, mode 2 the pieces of cells
+// that were first cut in global memory.
+struct UnitSource {
+  const int32_t *list;
+  const int32_t *count;
+  int32_t *next;
+  int mode;
+};
+
+// one unit: first sorted position, size, depth of its root
+__device__ __forceinline__ void unit_at(const Problem &P, const UnitSource &U, int t, int64_t &gb,
+                                        int &n, int &depth0) {
+  if (U.mode == 2) {
+    const int4 pc = P.pieces[t];
+    gb = pc.x;
+    n = pc.y - pc.x;
+    depth0 = pc.z;
+  } else {
+    const int c = U.list[t];
+    gb = P.cell_begin[c];
+    n = P.cell_begin[c + 1] - (int)gb;
+    depth0 = 0;
+  }
+}
+
+// The float small-cell teams are register-limited: keep 7, 6 and 5 CTAs per
+// SM for D <= 4, 5 and 6; the other instances are limited by shared memory.
+template <typename T, int D, int TEAM>
+constexpr int team_min_blocks() {
+  return (sizeof(T) == 4 && TEAM == 4) ? (D <= 4 ? 7 : (D == 5 ? 6 : 5)) : 1;
+}
+
+template <typename T, int D, int TEAM, bool VAR>
+__global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
+    team_kernel(Problem P, UnitSource U, int cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, tt = threadIdx.x;
+  constexpr int kThreads = 32 * TEAM;
+  WarpTile<T, D> S;
+  int *ctl;
+  {
+    unsigned char *base = smem_raw;
+    S.data = reinterpret_cast<T *>(base);
+    S.idx0 = reinterpret_cast<uint16_t *>(S.data + (size_t)(D + 1) * cap);
+    const size_t off =
+        ((size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t) + 15) &
+        ~size_t(15);
+    S.stk0 = reinterpret_cast<uint32_t *>(base + off);
+    S.top = reinterpret_cast<int *>(S.stk0 + stacks_entries(cap));
+    ctl = S.top + kClasses;
+    S.soff = reinterpret_cast<uint16_t *>(ctl + 1);
+    S.cap = cap;
+    if (tt < kClasses) {
+      int o = 0;
+      for (int c = 0; c < tt; ++c) o += class_capacity(c, cap);
+      S.soff[tt] = (uint16_t)o;
+      S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap);
+    }
+  }
+  const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
+  const int count = *U.count;
+  const int chunk = U.mode == 0 ? kWarpChunk : 1;
+  Counters cnt{0ull, 0ull, 0ull, 0ull};
+  unsigned long long merged = 0, passed = 0;
+
+  for (;;) {
+    if (tt == 0) ctl[0] = atomicAdd(U.next, chunk);
+    __syncthreads();
+    const int c0 = ctl[0];
+    __syncthreads();
+    if (c0 >= count) break;
+    const int c1 = min(c0 + chunk, count);
+    for (int t = c0; t < c1; ++t) {
+      int64_t gb;
+      int n, depth0;
+      unit_at(P, U, t, gb, n, depth0);
+      if (U.mode != 2 && (n <= P.n_min || n == 1)) {
+        // Sec. 3 "Input": cells with at most N_min particles are not merged
+        for (int i = tt; i < n; i += kThreads) {
+          const int src = orig_index(perm, gb, i);
+          P.perm_final[gb + i] = src;
+          P.head[gb + i] = kHeadSingle;
+#pragma unroll
+          for (int l = 0; l < D; ++l)
+            static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
+          static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+        }
+        passed += 1;
+        continue;
+      }
+      if (n > cap) {
+        if (tt == 0) set_error(P.err, kErrInternal);
+        continue;
+      }
+      if (U.mode != 2) merged += 1;
+      if (tt == 0) cnt.depth += (unsigned long long)depth0 * n;
+      if (t + 1 < c1 && !perm && tt < D + 1) {
+        // the next unit of this chunk: pull its columns into L2 meanwhile
+        int64_t nb;
+        int nn, nd;
+        unit_at(P, U, t + 1, nb, nn, nd);
+        const int64_t ne = nb + nn;
+        const size_t es = sizeof(T);
+        const char *col = static_cast<const char *>(tt < D ? P.q[tt] : P.w);
+        // the 16-byte-aligned part of the range only: never outside the array
+        const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nb * es) + 15) & ~uintptr_t(15);
+        const uintptr_t a1 = (reinterpret_cast<uintptr_t>(col + ne * es)) & ~uintptr_t(15);
+        if (a1 > a0)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0),
+                       "r"((unsigned)(a1 - a0))
+                       : "memory");
+      }
+      bool bad = false;
+#pragma unroll 4
+      for (int i = tt; i < n; i += kThreads) {
+        const int src = orig_index(perm, gb, i);
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const T x = StoreOf<T>::load(P.q[l], src);
+          bad |= !finite_val(x);
+          S.col(l)[i] = x;
+        }
+        const T w = StoreOf<T>::load(P.w, src);
+        bad |= !(w > T(0)) || !finite_val(w);
+        S.col(D)[i] = w;
+        S.idx(0)[i] = (uint16_t)i;
+      }
+      if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
+      if (tt < kClasses) S.top[tt] = 0;
+      __syncthreads();
+      if (tt == 0) {
+        if (n == 1) {
+          // a one-particle piece is final at once
+          emit_single<T, D>(P, S, perm, gb, 0, 0);
+          cnt.leaves += 1;
+        } else {
+          const int c = size_class(n);
+          S.stk(c)[0] = pack_rec(0, n, 0);
+          S.top[c] = 1;
+        }
+      }
+      // rounds: the team pops up to TEAM * 32/G subsets of the largest
+      // non-empty class; warp wt takes the wt-th share
+      for (;;) {
+        __syncthreads();
+        int c = -1;
+#pragma unroll
+        for (int k = kClasses - 1; k >= 0; --k)
+          if (c < 0 && S.top[k] > 0) c = k;
+        if (c < 0) break;
+        const int per = (c == 0) ? 32 : (32 >> (c - 1));
+        const int avail = S.top[c];
+        const int k = min(avail, TEAM * per);
+        const int kw = max(0, min(per, k - wt * per));
+        const int base = avail - 1 - wt * per;
+        __syncthreads();
+        if (tt == 0) S.top[c] = avail - k;
+        __syncthreads();
+        if (kw > 0) {
+          if (c == 0)
+            pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, base);
+          else
+            group_round<T, D, VAR>(P, S, perm, gb, c, lane, cnt, kw, base);
+        }
+        __syncwarp();
+      }
+      // the unit in final order: permutation, head bytes, staged particles
+      for (int i = tt; i < n; i += kThreads) {
+        const int j = S.idx(0)[i];
+        if (j >= n) {
+          // only after an internal failure left a position unmarked
+          set_error(P.err, kErrInternal);
+          P.perm_final[gb + i] = -1;
+          P.head[gb + i] = 0;
+          continue;
+        }
+        P.perm_final[gb + i] = orig_index(perm, gb, j);
+        P.head[gb + i] = (uint8_t)S.idx(1)[i];
+        stage<T, D>(P, S, gb + i, j);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) {
+    cnt.leaves += __shfl_xor_sync(0xffffffffu, cnt.leaves, m);
+    cnt.depth += __shfl_xor_sync(0xffffffffu, cnt.depth, m);
+    cnt.splits += __shfl_xor_sync(0xffffffffu, cnt.splits, m);
+    cnt.degenerate += __shfl_xor_sync(0xffffffffu, cnt.degenerate, m);
+  }
+  if (lane == 0) {
+    if (cnt.leaves) atomicAdd(&P.stats[kStLeaves], cnt.leaves);
+    if (cnt.depth) atomicAdd(&P.stats[kStDepth], cnt.depth);
+    if (cnt.splits) atomicAdd(&P.stats[kStSplits], cnt.splits);
+    if (cnt.degenerate) atomicAdd(&P.stats[kStDegenerate], cnt.degenerate);
+    if (wt == 0 && merged) atomicAdd(&P.stats[kStCellsMerged], merged);
+    if (wt == 0 && passed) atomicAdd(&P.stats[kStCellsPass], passed);
+  }
+}
+
+// ----------------------------------------------------------------- launch
+
+template <typename T>
+static size_t team_smem_t(int D, int cap) {
+  switch (D) {
+    case 2: return warp_region_bytes<T, 2>(cap);
+    case 3: return warp_region_bytes<T, 3>(cap);
+    case 4: return warp_region_bytes<T, 4>(cap);
+    case 5: return warp_region_bytes<T, 5>(cap);
+    default: return warp_region_bytes<T, 6>(cap);
+  }
+}
+
+template <typename T, int D, int TEAM, bool VAR>
+static cudaError_t launch_team_t(const Problem &P, const UnitSource &U, int cap, int grid,
+                                 cudaStream_t st) {
+  if (cap > kMaxCapW) return cudaErrorInvalidValue;
+  const size_t smem = warp_region_bytes<T, D>(cap);
+  // raise the dynamic shared-memory limit once per device (so that calls
+  // captured into a graph after a first eager call make no attribute change)
+  static int limit_set[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
+    e = cudaFuncSetAttribute(team_kernel<T, D, TEAM, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
+  }
+  team_kernel<T, D, TEAM, VAR><<<grid, 32 * TEAM, smem, st>>>(P, U, cap);
+  return cudaGetLastError();
+}
+
+template <typename T, int TEAM, bool VAR>
+static cudaError_t launch_team_d(const Problem &P, const UnitSource &U, int cap, int grid,
+                                 cudaStream_t st) {
+  switch (P.D) {
+    case 2: return launch_team_t<T, 2, TEAM, VAR>(P, U, cap, grid, st);
+    case 3: return launch_team_t<T, 3, TEAM, VAR>(P, U, cap, grid, st);
+    case 4: return launch_team_t<T, 4, TEAM, VAR>(P, U, cap, grid, st);
+    case 5: return launch_team_t<T, 5, TEAM, VAR>(P, U, cap, grid, st);
+    default: return launch_team_t<T, 6, TEAM, VAR>(P, U, cap, grid, st);
+  }
+}
+
+// all team launches of one decision build (precision, team size, D)
+template <bool VAR>
+static cudaError_t launch_team_build(const Problem &P, const UnitSource &U, int mixed,
+                                     int team, int cap, int grid, cudaStream_t st) {
+  if (team == 4)
+    return mixed ? launch_team_d<float, 4, VAR>(P, U, cap, grid, st)
+                 : launch_team_d<double, 4, VAR>(P, U, cap, grid, st);
+  return mixed ? launch_team_d<float, 8, VAR>(P, U, cap, grid, st)
+               : launch_team_d<double, 8, VAR>(P, U, cap, grid, st);
+}
+
+// the build with run-time decision variants (warp_var.cu)
+cudaError_t launch_team_variants(const Problem &P, const UnitSource &U, int mixed, int team,
+                                 int cap, int grid, cudaStream_t st);
+
+}  // namespace pma

@@ -20,13 +20,13 @@ from paper_1504_00636_gb300 import binding
 
 
 def run_gpu(p, precision="fp64", tol_x=None, tol_p=None, n_min=None, capacity=None,
-            shuffle_seed=None, merger=None):
+            shuffle_seed=None, merger=None, flags=0):
     import torch
     dev = torch.device("cuda", 0)
     dt = torch.float32 if precision == "mixed" else torch.float64
     n = p.n
     m = merger or binding.Merger(p.dx, p.dp, p.n_cells, capacity or max(n, 1), p.cell_size,
-                                 p.n_min if n_min is None else n_min, precision)
+                                 p.n_min if n_min is None else n_min, precision, flags)
     cells = torch.from_numpy(p.cell).to(dev)
     pos = [torch.from_numpy(np.ascontiguousarray(p.pos[a])).to(dev, dt) for a in range(p.dx)]
     mom = [torch.from_numpy(np.ascontiguousarray(p.mom[a])).to(dev, dt) for a in range(p.dp)]

@@ -1,0 +1,62 @@
+"""The decision variants (PMA_FLAG_SPLIT_NORMALIZED, PMA_FLAG_MOMENTUM_NORM)
+on the CUDA path against the oracle run with the same variant."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_00636_gb300 import binding, synth
+
+from parity import compare, conservation, local_index, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(binding.PMA_FLAG_SPLIT_NORMALIZED, oracle.VAR_NORMALIZED),
+            (binding.PMA_FLAG_MOMENTUM_NORM, oracle.VAR_PNORM),
+            (binding.PMA_FLAG_SPLIT_NORMALIZED | binding.PMA_FLAG_MOMENTUM_NORM,
+             oracle.VAR_NORMALIZED | oracle.VAR_PNORM)]
+IDS = ["normalized", "pnorm", "both"]
+WORKLOADS = [lambda: synth.counter_beams(),
+             lambda: synth.two_stream(cells=64),
+             lambda: synth.shower(grid=(20, 20), cap=9000)]
+WIDS = ["counter_beams", "two_stream_64", "shower_20x20"]
+
+
+@pytest.mark.parametrize("flags,variant", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("make", WORKLOADS, ids=WIDS)
+def test_fp64_variant_matches_oracle(make, flags, variant):
+    p = make()
+    # tolerances that make the normalised axis choice differ from the raw one
+    tx, tp = 0.3, 0.05
+    g = run_gpu(p, "fp64", tol_x=tx, tol_p=tp, flags=flags)
+    r = oracle.merge_particles(p, threads=8, tol_x=tx, tol_p=tp, variant=variant)
+    compare(p, g, r)
+    conservation(p, g)
+    assert g["stats"]["depth_sum"] == r.stats["depth_sum"] or r.flags.any()
+
+
+@pytest.mark.parametrize("flags,variant", VARIANTS, ids=IDS)
+@pytest.mark.parametrize("make", WORKLOADS, ids=WIDS)
+def test_mixed_variant_matches_oracle_on_rounded_inputs(make, flags, variant):
+    p = make().astype(np.float32)
+    tx, tp = 0.3, 0.05
+    g = run_gpu(p, "mixed", tol_x=tx, tol_p=tp, flags=flags)
+    r = oracle.merge_particles(p, threads=8, tol_x=tx, tol_p=tp, variant=variant)
+    gi = local_index(g["index"], p.cell, g["cell"], p.n_cells)
+    oi = local_index(r.index, p.cell, r.cell, p.n_cells)
+    diff = np.unique(p.cell[gi != oi])
+    unexplained = [c for c in diff if not r.flags[c]]
+    assert len(unexplained) <= max(1, 0.01 * np.unique(p.cell).size), unexplained[:10]
+    conservation(p, g)
+
+
+def test_variants_differ_from_the_literal_rule_on_gpu():
+    p = synth.counter_beams()
+    lit = run_gpu(p, "fp64")
+    pn = run_gpu(p, "fp64", flags=binding.PMA_FLAG_MOMENTUM_NORM)
+    # the momentum-norm CV stops transverse fragmentation near p_y = p_z = 0
+    assert pn["count"] < lit["count"] / 4
+
+
+def test_unknown_flags_are_rejected():
+    with pytest.raises(binding.PmaError):
+        binding.Merger(1, 3, 4, 16, flags=8)
