@@ -37,6 +37,9 @@ NEAR_CUT = 4
 # VAR_PNORM       momentum CVs use |P| (length of the mean momentum vector)
 VAR_NORMALIZED = 2
 VAR_PNORM = 4
+# Step 7 variant: sets of m >= 3 become two particles that also conserve the
+# total energy sum w sqrt(1 + |p|^2) (see pma_oracle.c)
+VAR_CONSERVE_ENERGY = 8
 
 _ERRORS = {1: "invalid argument", 2: "invalid input", 3: "out of memory"}
 

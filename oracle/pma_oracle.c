@@ -39,6 +39,21 @@
  *                       Delta_l = sigma_l / |P| with |P| = sqrt(sum_l P_l^2)
  *                       over the momentum axes, instead of |P_l|.
  * The near-tie flags then refer to the values that the variant compares.
+ *
+ * Optional energy-conserving replacement (ORC_VAR_CONSERVE_ENERGY; the paper
+ * only names the idea of merging into two particles, Sec. 3, remark on
+ * energy; the rule below is derived here from the conservation laws): a
+ * final set of m >= 3 particles becomes two particles of weight W/2 at the
+ * centroid X with momenta P + d and P - d.  They keep W, W P and the total
+ * energy E = sum w sqrt(1 + |p|^2) when |P + d| = |P - d| = sqrt(g^2 - 1),
+ * g = E / W: d orthogonal to P with |d|^2 = g^2 - 1 - |P|^2, which is >= 0
+ * because sqrt(1 + |p|^2) is convex.  Its direction is the momentum axis e_k
+ * with the largest sigma_k^2 (1 - Phat_k^2) (Phat = P / |P|, 0 for P = 0),
+ * made orthogonal to P; when every such value is 0, the axis with the
+ * smallest |P_k|.  With one momentum axis d is along P instead: P +- u with
+ * u^2 = g^2 (g^2 - 1 - P^2) / (g^2 - P^2) (from sqrt(1 + (P + u)^2) +
+ * sqrt(1 + (P - u)^2) = 2 g).  Sets of one or two particles are copied
+ * verbatim; the members of a set map to its first output.
  */
 #include <float.h>
 #include <math.h>
@@ -61,6 +76,7 @@
 
 #define ORC_VAR_NORMALIZED 2u
 #define ORC_VAR_PNORM 4u
+#define ORC_VAR_CONSERVE_ENERGY 8u
 
 typedef struct {
     int dx, dp, D;
@@ -308,7 +324,7 @@ static int setup_problem(orc_problem *P, int dx, int dp, const double *pos,
 {
     if (dx < 1 || dx > 3 || dp < 1 || dp > 3)
         return ORC_ERR_ARG;
-    if (variant & ~(ORC_VAR_NORMALIZED | ORC_VAR_PNORM))
+    if (variant & ~(ORC_VAR_NORMALIZED | ORC_VAR_PNORM | ORC_VAR_CONSERVE_ENERGY))
         return ORC_ERR_ARG;
     P->variant = variant;
     if (!(tol_x >= 0.0) || !(tol_p >= 0.0) || isinf(tol_x) || isinf(tol_p))
@@ -484,6 +500,69 @@ static double kinetic(const orc_problem *P, int64_t i, const double *const *mom)
     return sqrt(1.0 + p2) - 1.0;
 }
 
+/* ORC_VAR_CONSERVE_ENERGY: the two momenta a, b that replace the set ids[ms]
+ * (ms >= 3) with weight W and centroid momentum Pm (see the header). */
+static void energy_pair(const orc_problem *P, const int64_t *ids, int64_t ms, double W,
+                        const double *Pm, double *a, double *b)
+{
+    const int dp = P->dp, dx = P->dx;
+    double E = 0.0;
+    for (int64_t i = 0; i < ms; ++i) {
+        double p2 = 0.0;
+        for (int l = 0; l < dp; ++l)
+            p2 += P->q[dx + l][ids[i]] * P->q[dx + l][ids[i]];
+        E += P->w[ids[i]] * sqrt(1.0 + p2);
+    }
+    double g = E / W;
+    double P2 = 0.0;
+    for (int l = 0; l < dp; ++l)
+        P2 += Pm[l] * Pm[l];
+    if (dp == 1) {
+        double u2 = g * g * (g * g - 1.0 - P2) / (g * g - P2);
+        double u = sqrt(u2 > 0.0 ? u2 : 0.0);
+        a[0] = Pm[0] + u;
+        b[0] = Pm[0] - u;
+        return;
+    }
+    double nP = sqrt(P2), ph[3] = {0.0, 0.0, 0.0};
+    if (nP > 0.0)
+        for (int l = 0; l < dp; ++l)
+            ph[l] = Pm[l] / nP;
+    /* sigma_k^2, two-pass about the centroid */
+    int k = -1;
+    double best = 0.0;
+    for (int l = 0; l < dp; ++l) {
+        double v = 0.0;
+        for (int64_t i = 0; i < ms; ++i) {
+            double d = P->q[dx + l][ids[i]] - Pm[l];
+            v += P->w[ids[i]] * d * d;
+        }
+        double score = (v / W) * (1.0 - ph[l] * ph[l]);
+        if (score > best) {
+            best = score;
+            k = l;
+        }
+    }
+    if (k < 0) {
+        k = 0;
+        for (int l = 1; l < dp; ++l)
+            if (fabs(Pm[l]) < fabs(Pm[k]))
+                k = l;
+    }
+    /* e_k minus its component along P, normalised */
+    double dir[3], n2 = 0.0;
+    for (int l = 0; l < dp; ++l) {
+        dir[l] = (l == k ? 1.0 : 0.0) - ph[k] * ph[l];
+        n2 += dir[l] * dir[l];
+    }
+    double d2 = g * g - 1.0 - P2;
+    double s = sqrt(d2 > 0.0 ? d2 : 0.0) / sqrt(n2);
+    for (int l = 0; l < dp; ++l) {
+        a[l] = Pm[l] + s * dir[l];
+        b[l] = Pm[l] - s * dir[l];
+    }
+}
+
 /*
  * Merge every cell.  Inputs: n particles, cell[n] in [0, n_cells), SoA
  * pos[dx][n], mom[dp][n] and w[n] (w > 0, all finite), cell_size[dx],
@@ -567,27 +646,59 @@ int pma_oracle_merge(int64_t n, const int32_t *cell, int dx, int dp,
     int64_t M = 0;
     const double *momp[3] = {mom, mom + n, mom + 2 * n};
     double e_in = 0.0, e_out = 0.0;
+    const int ec = (variant & ORC_VAR_CONSERVE_ENERGY) != 0;
     for (int64_t c = 0; c < n_cells; ++c) {
         int64_t b = cell_begin[c], m = cell_begin[c + 1] - b;
+        int64_t i0 = 0;  /* the leaves' members are consecutive in order[] */
         for (int64_t j = 0; j < n_leaves[c]; ++j) {
             const orc_leaf *L = &leaves[b + j];
-            if (out_cell) out_cell[M + j] = (int32_t)c;
-            if (out_w) out_w[M + j] = L->W;
-            for (int l = 0; l < dx; ++l)
-                if (out_pos) out_pos[(int64_t)l * n + M + j] = L->c[l];
-            double p2 = 0.0;
-            for (int l = 0; l < dp; ++l) {
-                if (out_mom) out_mom[(int64_t)l * n + M + j] = L->c[dx + l];
-                p2 += L->c[dx + l] * L->c[dx + l];
+            int64_t i1 = i0;
+            while (i1 < m && leaf_of[b + i1] == j)
+                ++i1;
+            const int64_t ms = i1 - i0;
+            /* the outputs of this leaf: 1, or 2 with ORC_VAR_CONSERVE_ENERGY */
+            double ow[2], oc[2][ORC_MAXD];
+            int nout = 1;
+            ow[0] = L->W;
+            for (int l = 0; l < P.D; ++l)
+                oc[0][l] = L->c[l];
+            if (ec && ms == 2) {
+                nout = 2;
+                for (int t = 0; t < 2; ++t) {
+                    int64_t id = order[b + i0 + t];
+                    ow[t] = w[id];
+                    for (int l = 0; l < P.D; ++l)
+                        oc[t][l] = P.q[l][id];
+                }
+            } else if (ec && ms >= 3) {
+                nout = 2;
+                ow[0] = ow[1] = 0.5 * L->W;
+                for (int l = 0; l < dx; ++l)
+                    oc[1][l] = L->c[l];
+                energy_pair(&P, order + b + i0, ms, L->W, L->c + dx, oc[0] + dx, oc[1] + dx);
             }
-            e_out += L->W * (sqrt(1.0 + p2) - 1.0);
+            for (int t = 0; t < nout; ++t) {
+                if (out_cell) out_cell[M + t] = (int32_t)c;
+                if (out_w) out_w[M + t] = ow[t];
+                for (int l = 0; l < dx; ++l)
+                    if (out_pos) out_pos[(int64_t)l * n + M + t] = oc[t][l];
+                double p2 = 0.0;
+                for (int l = 0; l < dp; ++l) {
+                    if (out_mom) out_mom[(int64_t)l * n + M + t] = oc[t][dx + l];
+                    p2 += oc[t][dx + l] * oc[t][dx + l];
+                }
+                e_out += ow[t] * (sqrt(1.0 + p2) - 1.0);
+            }
+            for (int64_t i = i0; i < i1; ++i) {
+                int64_t id = order[b + i];
+                /* a verbatim pair keeps one output per member */
+                int64_t slot = (ec && ms == 2) ? M + (i - i0) : M;
+                if (out_index) out_index[id] = (int32_t)slot;
+                e_in += w[id] * kinetic(&P, id, momp);
+            }
+            M += nout;
+            i0 = i1;
         }
-        for (int64_t i = 0; i < m; ++i) {
-            int64_t id = order[b + i];
-            if (out_index) out_index[id] = (int32_t)(M + leaf_of[b + i]);
-            e_in += w[id] * kinetic(&P, id, momp);
-        }
-        M += n_leaves[c];
     }
     *out_count = M;
     if (stats) {

@@ -87,6 +87,34 @@ def pin_failures(lib):
     t = oracle.trace(xs, ps, np.ones(4), tol_x=0.0, tol_p=1.0, lib=lib,
                      variant=oracle.VAR_NORMALIZED)
     check("normalized_zero_tol", t.axis[0] == 0)
+    # energy-conserving replacement: hand-worked set (|d|^2 = 23/45 along y)
+    EC = oracle.VAR_CONSERVE_ENERGY
+    z3 = np.zeros(3, np.int32)
+    mom = np.array([[0.75, 2.4, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    r = oracle.merge(z3, np.array([[0.2, 0.5, 0.8]]), mom, np.ones(3), 1, tol_x=1.0,
+                     tol_p=1.0, lib=lib, variant=EC)
+    d = math.sqrt(23.0 / 45.0)
+    check("ec_hand", r.count == 2 and np.allclose(r.mom[1], [d, -d], rtol=1e-13))
+
+    def total_energy(w_, m_):
+        return float(np.sum(w_ * np.sqrt(1.0 + np.sum(m_ ** 2, axis=0))))
+
+    p = synth.two_stream(cells=4)
+    r = oracle.merge_particles(p, lib=lib, variant=EC)
+    e_in, e_out = total_energy(p.w, p.mom), total_energy(r.w, r.mom)
+    check("ec_energy", abs(e_out - e_in) <= 1e-12 * e_in and r.count > 0)
+    rng = np.random.default_rng(3)
+    m1 = rng.normal(0.5, 0.2, size=(1, 9))
+    w1 = rng.uniform(0.5, 1.5, 9)
+    r = oracle.merge(np.zeros(9, np.int32), rng.random((1, 9)), m1, w1, 1, tol_x=1.0,
+                     tol_p=1e9, lib=lib, variant=EC)
+    check("ec_one_axis", r.count == 2 and
+          abs(total_energy(r.w, r.mom) - total_energy(w1, m1)) <= 1e-12 * total_energy(w1, m1))
+    mom = np.array([[1.0, 2.0, 1.5, 1.5], [0.2, 0.2, 0.2, 0.2], [0.05, 0.05, 0.2, -0.1]])
+    r = oracle.merge(np.zeros(4, np.int32), np.full((1, 4), 0.5), mom, np.ones(4), 1,
+                     tol_x=1.0, tol_p=1e9, lib=lib, variant=EC)
+    dd = r.mom[:, 0] - mom.mean(axis=1) if r.count == 2 else np.zeros(3)
+    check("ec_direction", r.count == 2 and abs(dd[2]) > 0.99 * np.linalg.norm(dd))
     return fails
 
 
@@ -111,6 +139,13 @@ MUTANTS = {
                       "double scale = fabs(M->Q[l]);"),
     "normalized_ignores_T": ("return d / T;", "return d;"),
     "normalized_zero_tol": ("return d > 0.0 ? INFINITY : 0.0;", "return 0.0;"),
+    "ec_no_orthogonalization": ("dir[l] = (l == k ? 1.0 : 0.0) - ph[k] * ph[l];",
+                                "dir[l] = (l == k ? 1.0 : 0.0);"),
+    "ec_kinetic_mean": ("E += P->w[ids[i]] * sqrt(1.0 + p2);",
+                        "E += P->w[ids[i]] * (sqrt(1.0 + p2) - 1.0);"),
+    "ec_raw_variance": ("double score = (v / W) * (1.0 - ph[l] * ph[l]);",
+                        "double score = (v / W);"),
+    "ec_one_axis_sign": ("(g * g - 1.0 - P2) / (g * g - P2)", "(g * g - 1.0 - P2) / (g * g + P2)"),
 }
 
 

@@ -173,4 +173,4 @@ def test_unknown_variant_bits_are_rejected():
     with pytest.raises(ValueError):
         oracle.merge_particles(p, variant=1)
     with pytest.raises(ValueError):
-        oracle.merge_particles(p, variant=8)
+        oracle.merge_particles(p, variant=16)
