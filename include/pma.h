@@ -64,10 +64,27 @@ extern "C" {
  *       vector: Delta_l = sigma_l / |P|, |P| = sqrt(sum over momentum axes
  *       of P_l^2), instead of sigma_l / |P_l|.  Sets whose mean momentum is
  *       near zero on one axis then stop splitting on that axis.
- * Both apply to pma_merge and pma_merge_host; pma_merge_noalloc ignores them.
+ * They apply to pma_merge and pma_merge_host; pma_merge_noalloc ignores them.
  */
 #define PMA_FLAG_SPLIT_NORMALIZED 2u
 #define PMA_FLAG_MOMENTUM_NORM 4u
+/*
+ * Energy-conserving replacement (Step 7 variant; the paper names the idea
+ * of merging into two particles in its remark on energy, Sec. 3, without a
+ * rule; this rule follows from the conservation laws).  A final set of
+ * m >= 3 particles with weight W, centroid X, P and total energy
+ * E = sum w sqrt(1 + |p|^2) (p in units of m c) becomes two particles of
+ * weight W/2 at X with momenta P + d and P - d, |P +- d|^2 = g^2 - 1,
+ * g = E / W: d is orthogonal to P with |d|^2 = g^2 - 1 - |P|^2 (>= 0 by
+ * convexity), along the momentum axis e_k of largest sigma_k^2 (1 - Phat_k^2)
+ * made orthogonal to P (the axis of smallest |P_k| if all are 0).  With one
+ * momentum axis d is along P: d^2 = g^2 (g^2 - 1 - P^2) / (g^2 - P^2).  Sets
+ * of two particles are copied as they are, the lower input index first.
+ * W, W P and E are conserved to rounding.  out->index maps the members of a
+ * set to its first output (a copied pair: each member to its own).  The
+ * output count M is still <= n.
+ */
+#define PMA_FLAG_CONSERVE_ENERGY 8u
 
 typedef struct pma_handle pma_handle;
 

@@ -53,7 +53,8 @@
  * smallest |P_k|.  With one momentum axis d is along P instead: P +- u with
  * u^2 = g^2 (g^2 - 1 - P^2) / (g^2 - P^2) (from sqrt(1 + (P + u)^2) +
  * sqrt(1 + (P - u)^2) = 2 g).  Sets of one or two particles are copied
- * verbatim; the members of a set map to its first output.
+ * verbatim (a pair in ascending input index); the members of a larger set
+ * map to its first output.
  */
 #include <float.h>
 #include <math.h>
@@ -664,8 +665,10 @@ int pma_oracle_merge(int64_t n, const int32_t *cell, int dx, int dp,
                 oc[0][l] = L->c[l];
             if (ec && ms == 2) {
                 nout = 2;
+                int64_t lo = order[b + i0], hi = order[b + i0 + 1];
+                if (hi < lo) { int64_t tmp = lo; lo = hi; hi = tmp; }
                 for (int t = 0; t < 2; ++t) {
-                    int64_t id = order[b + i0 + t];
+                    int64_t id = t == 0 ? lo : hi;
                     ow[t] = w[id];
                     for (int l = 0; l < P.D; ++l)
                         oc[t][l] = P.q[l][id];
@@ -691,8 +694,10 @@ int pma_oracle_merge(int64_t n, const int32_t *cell, int dx, int dp,
             }
             for (int64_t i = i0; i < i1; ++i) {
                 int64_t id = order[b + i];
-                /* a verbatim pair keeps one output per member */
-                int64_t slot = (ec && ms == 2) ? M + (i - i0) : M;
+                /* a verbatim pair keeps one output per member, the lower
+                   input index first */
+                int64_t other = order[b + (i == i0 ? i0 + 1 : i0)];
+                int64_t slot = (ec && ms == 2) ? M + (id > other ? 1 : 0) : M;
                 if (out_index) out_index[id] = (int32_t)slot;
                 e_in += w[id] * kinetic(&P, id, momp);
             }

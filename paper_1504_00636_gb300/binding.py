@@ -29,6 +29,7 @@ PMA_MIXED = 1
 PMA_FLAG_NO_INDEX = 1
 PMA_FLAG_SPLIT_NORMALIZED = 2
 PMA_FLAG_MOMENTUM_NORM = 4
+PMA_FLAG_CONSERVE_ENERGY = 8
 
 SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
            "pma_set_timing", "pma_get_timing", "pma_merge_noalloc", "pma_destroy",

@@ -196,7 +196,8 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   if (cfg->n_min < 0) return PMA_ERR_INVALID_ARG;
   if (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED) return PMA_ERR_INVALID_ARG;
   if (cfg->capacity < 0 || cfg->capacity > INT32_MAX) return PMA_ERR_INVALID_ARG;
-  if (cfg->flags & ~(PMA_FLAG_NO_INDEX | PMA_FLAG_SPLIT_NORMALIZED | PMA_FLAG_MOMENTUM_NORM))
+  if (cfg->flags & ~(PMA_FLAG_NO_INDEX | PMA_FLAG_SPLIT_NORMALIZED | PMA_FLAG_MOMENTUM_NORM |
+                     PMA_FLAG_CONSERVE_ENERGY))
     return PMA_ERR_INVALID_ARG;
   for (int a = 0; a < cfg->dx; ++a)
     if (!(cfg->cell_size[a] > 0.0) || !std::isfinite(cfg->cell_size[a]))
@@ -409,6 +410,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.dx = h->cfg.dx;
   m.dp = h->cfg.dp;
   m.mixed = h->mixed;
+  m.ec = (h->cfg.flags & PMA_FLAG_CONSERVE_ENERGY) ? 1 : 0;
   m.head = h->head;
   m.perm_final = h->perm_final;
   m.cells = cells;

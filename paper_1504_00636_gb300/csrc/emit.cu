@@ -12,6 +12,10 @@
 //                  staged members (a product of two floats is exact in FP64).
 //                  The tile's staged columns reach shared memory by bulk
 //                  asynchronous copies while the CTA scans the head bytes.
+// With the energy-conserving option (EC) a head of a set of m >= 2 particles
+// takes two output slots: a set of two is copied as it is, and a larger set
+// becomes two particles of weight W/2 at X with momenta P + d and P - d that
+// also keep the total energy sum w sqrt(1 + |p|^2); see energy_set below.
 #include "lookback.cuh"
 #include "pma_launch.h"
 
@@ -55,10 +59,29 @@ __device__ __forceinline__ unsigned head_mask(unsigned hw) {
   return mask;
 }
 
+// output slots of a head byte: 1 for a single particle, 1 (or 2 with EC) for
+// a merged set, 0 inside a set
+template <bool EC>
+__device__ __forceinline__ int head_slots(unsigned h) {
+  return h == 0u ? 0 : ((EC && h != (unsigned)kHeadSingle) ? 2 : 1);
+}
+
+// output slots of the first `upto` of a thread's 4 consecutive positions
+template <bool EC>
+__device__ __forceinline__ int chunk_slots(unsigned hw, int upto) {
+  if (!EC) return __popc(head_mask(hw) & ((1u << upto) - 1u));
+  int v = 0;
+#pragma unroll
+  for (int j = 0; j < kEmitChunk; ++j)
+    if (j < upto) v += head_slots<true>((hw >> (8 * j)) & 0xffu);
+  return v;
+}
+
+template <bool EC>
 __global__ void __launch_bounds__(kEmitThreads) count_kernel(EmitArgs a) {
   __shared__ int s_warp[32];
   const int64_t c0 = (int64_t)blockIdx.x * kEmitTile + (int64_t)threadIdx.x * kEmitChunk;
-  int v = __popc(head_mask(load_heads(a.head, c0, a.n)));
+  int v = chunk_slots<EC>(load_heads(a.head, c0, a.n), kEmitChunk);
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
@@ -148,12 +171,140 @@ size_t emit_smem_bytes(int D, int mixed) {
   return (size_t)(D + 1) * kEmitTile * (mixed ? 4 : 8) + (size_t)kEmitTile * 4;
 }
 
+// EC: one final set of m >= 2 members at positions [p, e) of the staged
+// arrays (in this tile's shared memory below t0 + cnt, else in global
+// memory), first output slot `slot`.  m = 2: both members as they are.
+// m >= 3: W/2 at X twice, momenta P + d and P - d with g = E / W,
+// E = sum w sqrt(1 + |p|^2): d across P with |d|^2 = g^2 - 1 - |P|^2 along
+// the momentum axis of largest sigma_k^2 (1 - Phat_k^2) made orthogonal to P
+// (the axis of smallest |P_k| when all are 0); one momentum axis: d along P
+// with d^2 = g^2 (g^2 - 1 - P^2) / (g^2 - P^2).  The members map to the first
+// slot (a pair: each to its own, the lower input index first).
+template <typename T>
+__device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_perm,
+                           int64_t t0, int cnt, int64_t p, int64_t e, long long slot) {
+  const int D = a.dx + a.dp;
+  auto raw = [&](int l, int64_t r) -> T {
+    return r < t0 + cnt ? s_col[l * kEmitTile + (int)(r - t0)]
+                        : static_cast<const T *>(a.fin[l])[r];
+  };
+  auto orig = [&](int64_t r) -> int { return r < t0 + cnt ? s_perm[r - t0] : a.perm_final[r]; };
+  if (e - p == 2) {
+    const bool swap = orig(p + 1) < orig(p);
+    for (int t = 0; t < 2; ++t) {
+      const int64_t r = p + (t ^ (int)swap);
+      const int o = orig(r);
+      if (a.out_index && (unsigned)o < (unsigned)a.n) a.out_index[o] = (int32_t)(slot + t);
+      for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot + t] = raw(l, r);
+      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot + t] = to_f64<T>(raw(a.dx + l, r));
+      a.out_w[slot + t] = to_f64<T>(raw(D, r));
+    }
+    return;
+  }
+  // pass 1: W, sum w x, sum w p (the momentum axes as 0..2), total energy
+  double W = 0.0, E = 0.0, SX[3] = {0.0, 0.0, 0.0}, SP[3] = {0.0, 0.0, 0.0};
+  for (int64_t r = p; r < e; ++r) {
+    const double w = to_f64<T>(raw(D, r));
+    double p2 = 0.0;
+    W += w;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      if (l < a.dx) SX[l] = fma(w, to_f64<T>(raw(l, r)), SX[l]);
+      if (l < a.dp) {
+        const double q = to_f64<T>(raw(a.dx + l, r));
+        SP[l] = fma(w, q, SP[l]);
+        p2 = fma(q, q, p2);
+      }
+    }
+    E = fma(w, sqrt(1.0 + p2), E);
+    const int o = orig(r);
+    if (a.out_index && (unsigned)o < (unsigned)a.n) a.out_index[o] = (int32_t)slot;
+  }
+  const double inv = 1.0 / W;
+  double Pm[3] = {0.0, 0.0, 0.0}, P2 = 0.0;
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+    if (l < a.dp) {
+      Pm[l] = SP[l] * inv;
+      P2 = fma(Pm[l], Pm[l], P2);
+    }
+  const double g = E * inv;
+  double da[3] = {0.0, 0.0, 0.0};
+  if (a.dp == 1) {
+    const double u2 = g * g * (g * g - 1.0 - P2) / (g * g - P2);
+    da[0] = sqrt(fmax(u2, 0.0));
+  } else {
+    const double nP = sqrt(P2);
+    double ph[3] = {0.0, 0.0, 0.0};
+    if (nP > 0.0) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) ph[l] = Pm[l] / nP;
+    }
+    // pass 2: sigma_k^2 about the centroid, scored across P
+    double var[3] = {0.0, 0.0, 0.0};
+    for (int64_t r = p; r < e; ++r) {
+      const double w = to_f64<T>(raw(D, r));
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        if (l < a.dp) {
+          const double dq = to_f64<T>(raw(a.dx + l, r)) - Pm[l];
+          var[l] = fma(w * dq, dq, var[l]);
+        }
+    }
+    int k = -1;
+    double best = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (l < a.dp) {
+        const double sc = (var[l] * inv) * (1.0 - ph[l] * ph[l]);
+        if (sc > best) {
+          best = sc;
+          k = l;
+        }
+      }
+    if (k < 0) {
+      k = 0;
+      double pk = fabs(Pm[0]);
+#pragma unroll
+      for (int l = 1; l < 3; ++l)
+        if (l < a.dp && fabs(Pm[l]) < pk) {
+          pk = fabs(Pm[l]);
+          k = l;
+        }
+    }
+    double phk = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      if (l == k) phk = ph[l];
+    double dir[3], n2 = 0.0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      dir[l] = (l == k ? 1.0 : 0.0) - phk * ph[l];
+      if (l < a.dp) n2 = fma(dir[l], dir[l], n2);
+    }
+    const double sc = sqrt(fmax(g * g - 1.0 - P2, 0.0)) / sqrt(n2);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) da[l] = sc * dir[l];
+  }
+  const double Wh = 0.5 * W;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const long long s = slot + t;
+    a.out_w[s] = Wh;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      if (l < a.dx) static_cast<T *>(a.out_pos[l])[s] = (T)(SX[l] * inv);
+      if (l < a.dp) a.out_mom[l][s] = t == 0 ? Pm[l] + da[l] : Pm[l] - da[l];
+    }
+  }
+}
+
 // One CTA per tile of 1024 final positions.  One thread starts bulk copies of
 // the tile's staged columns and final permutation into shared memory; the
 // CTA meanwhile reads the head bytes and scans them into output slots.  The
 // positions are then handled in consecutive order across the threads, so the
 // output stores of runs of one-particle sets are coalesced.
-template <typename T>
+template <typename T, bool EC>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_bar;
@@ -186,7 +337,8 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   const unsigned mask = head_mask(hw);
   reinterpret_cast<unsigned *>(s_head)[tid] = hw;
   int total;
-  const int ex = block_exclusive_scan(__popc(mask), s_warp, &total);  // barriers: s_bar is set up
+  // barriers inside: s_bar is set up
+  const int ex = block_exclusive_scan(chunk_slots<EC>(hw, kEmitChunk), s_warp, &total);
   s_mask[tid] = (unsigned short)mask;
   s_chunk[tid] = ex;
   const long long prefix = a.tile_prefix[blockIdx.x];
@@ -204,18 +356,27 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     const int off = j * kEmitThreads + tid;
     if (off >= cnt) break;
     const int ch = off / kEmitChunk, in = off % kEmitChunk;
-    const unsigned m = s_mask[ch];
-    const long long slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
-    const int orig = s_perm[off];
     const int h = s_head[off];
+    if (EC && h == 0) continue;  // members of merged sets: handled with their set
+    long long slot;
+    if (EC) {
+      slot = prefix + s_chunk[ch] +
+             chunk_slots<true>(reinterpret_cast<const unsigned *>(s_head)[ch], in);
+    } else {
+      const unsigned m = s_mask[ch];
+      slot = prefix + s_chunk[ch] + __popc(m & ((2u << in) - 1u)) - 1;
+    }
+    const int orig = s_perm[off];
     if ((unsigned)orig >= (unsigned)a.n) {
       // a position left unwritten by an earlier failure: never follow it
       internal = true;
       continue;
     }
-    if (a.out_index) a.out_index[orig] = (int32_t)slot;
+    if (a.out_index && (!EC || h == kHeadSingle)) a.out_index[orig] = (int32_t)slot;
     if (!h) continue;
-    a.out_cell[slot] = a.cells[sorted ? t0 + off : (int64_t)orig];
+    const int32_t cell_id = a.cells[sorted ? t0 + off : (int64_t)orig];
+    a.out_cell[slot] = cell_id;
+    if (EC && h != kHeadSingle) a.out_cell[slot + 1] = cell_id;
     if (h == kHeadSingle) {
       // one-particle set: the particle itself (Step 7)
 #pragma unroll
@@ -260,6 +421,10 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       internal = true;
       e = a.n;
     }
+    if (EC) {
+      energy_set<T>(a, s_col, s_perm, t0, cnt, t0 + off, e, slot_m);
+      continue;
+    }
     double W = 0.0, S1[kMaxD];
 #pragma unroll
     for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
@@ -298,7 +463,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   if (internal) atomicOr(a.err, kErrInternal);
 }
 
-template <typename T>
+template <typename T, bool EC>
 static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   const size_t smem = emit_smem_bytes(a.dx + a.dp, sizeof(T) == 4);
   // raise the dynamic shared-memory limit once per device
@@ -307,21 +472,24 @@ static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
-    e = cudaFuncSetAttribute(emit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(emit_kernel<T, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
   }
-  emit_kernel<T><<<a.tiles, kEmitThreads, smem, st>>>(a);
+  emit_kernel<T, EC><<<a.tiles, kEmitThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
   if (a.tiles <= 0) return cudaSuccess;
-  count_kernel<<<a.tiles, kEmitThreads, 0, st>>>(a);
+  if (a.ec)
+    count_kernel<true><<<a.tiles, kEmitThreads, 0, st>>>(a);
+  else
+    count_kernel<false><<<a.tiles, kEmitThreads, 0, st>>>(a);
   tiles_kernel<<<1, kScanCta, 0, st>>>(a);
-  cudaError_t e = a.mixed ? launch_emit_t<float>(a, st) : launch_emit_t<double>(a, st);
-  return e;
+  if (a.ec) return a.mixed ? launch_emit_t<float, true>(a, st) : launch_emit_t<double, true>(a, st);
+  return a.mixed ? launch_emit_t<float, false>(a, st) : launch_emit_t<double, false>(a, st);
 }
 
 }  // namespace pma

@@ -63,6 +63,7 @@ void radix_plan(BinArgs &a);
 struct EmitArgs {
   int64_t n;
   int32_t dx, dp, mixed;
+  int32_t ec;  // energy-conserving replacement (PMA_FLAG_CONSERVE_ENERGY)
   const uint8_t *head;
   const int32_t *perm_final;
   const int32_t *cells;

@@ -146,3 +146,17 @@ def test_energy_mode_changes_only_step7():
     assert ec.stats["splits"] == lit.stats["splits"]
     assert ec.stats["leaves"] == lit.stats["leaves"]
     assert ec.count >= lit.count
+
+
+def test_copied_pair_comes_out_in_input_order():
+    # x = 0.9, 0.1, 0.8: the cut on x leaves {1} and the pair {0, 2}, which
+    # stays whole (tol_x 0.1 > its Delta_x 0.05); the pair is copied with the
+    # lower input index first
+    pos = np.array([[0.9, 0.1, 0.8]])
+    mom = np.full((1, 3), 1.0)
+    w = np.array([1.0, 2.0, 3.0])
+    r = oracle.merge(np.zeros(3, np.int32), pos, mom, w, 1, tol_x=0.1, tol_p=0.1, variant=EC)
+    assert r.count == 3
+    assert list(r.index) == [1, 0, 2]
+    np.testing.assert_array_equal(r.w, [2.0, 1.0, 3.0])
+    np.testing.assert_array_equal(r.pos[0], [0.1, 0.9, 0.8])
