@@ -12,6 +12,8 @@
 //               bits, gives the permutation sorted position -> input index
 //               in (cell, input index) order, so the result does not depend
 //               on how the GPU schedules the work.
+#include <climits>
+
 #include "lookback.cuh"
 #include "pma_launch.h"
 
@@ -23,27 +25,53 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 int scan_tiles_for(int64_t n) { return (int)((n + kScanTile - 1) / kScanTile); }
 
-__global__ void hist_kernel(BinArgs a) {
+constexpr int kHistRows = 4;  // rows of 32 ids a warp loads per step
+
+// Each warp reads kHistRows rows of 32 consecutive ids at a time.  Inside a
+// row, every run of equal valid ids adds its length to the cell's count with
+// one atomic (run starts from a neighbour shuffle and one ballot), so ids
+// grouped by cell cost one atomic per run; ungrouped ids stay correct (runs
+// of one).  A pair of neighbours in decreasing order marks the input as not
+// grouped.
+__global__ void __launch_bounds__(256) hist_kernel(BinArgs a) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int unsorted = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.n;
-       base += stride) {
-    int64_t i = base + lane;
-    int c = -1;
-    if (i < a.n) {
-      c = a.cells[i];
-      if (c < 0 || c >= a.n_cells) {
-        atomicOr(a.err, kErrInput);
-        c = -1;
-      } else if (i > 0 && a.cells[i - 1] > c) {
-        unsorted = 1;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t step = 32 * kHistRows;
+  bool unsorted = false, bad = false;
+  for (int64_t w0 = warp * step; w0 < a.n; w0 += warps * step) {  // warp-uniform
+    int c[kHistRows];
+#pragma unroll
+    for (int j = 0; j < kHistRows; ++j) {
+      const int64_t i = w0 + j * 32 + lane;
+      c[j] = i < a.n ? a.cells[i] : -1;
+    }
+    int carry = (lane == 0 && w0 > 0) ? a.cells[w0 - 1] : INT_MIN;  // the id before the row
+#pragma unroll
+    for (int j = 0; j < kHistRows; ++j) {
+      const int64_t i = w0 + j * 32 + lane;
+      const int v = c[j];
+      const bool in = i < a.n;
+      const bool valid = in && v >= 0 && v < a.n_cells;
+      bad |= in && !valid;
+      int prev = __shfl_up_sync(full, v, 1);
+      if (lane == 0) prev = carry;
+      if (valid && prev > v) unsorted = true;
+      carry = __shfl_sync(full, v, 31);
+      const int key = valid ? v : -1;
+      const int kprev = __shfl_up_sync(full, key, 1);
+      const bool start = lane == 0 || kprev != key;
+      const unsigned starts = __ballot_sync(full, start);
+      if (start && key >= 0) {
+        const unsigned later = starts & ~((2u << lane) - 1u);
+        const int end = later ? __ffs(later) - 1 : 32;
+        atomicAdd(&a.counts[key], end - lane);
       }
     }
-    unsigned grp = __match_any_sync(0xffffffffu, c);
-    if (c >= 0 && lane == __ffs(grp) - 1) atomicAdd(&a.counts[c], __popc(grp));
   }
-  if (__any_sync(0xffffffffu, unsorted) && lane == 0) atomicExch(a.unsorted, 1);
+  if (__any_sync(full, bad) && lane == 0) atomicOr(a.err, kErrInput);
+  if (__any_sync(full, unsorted) && lane == 0) atomicExch(a.unsorted, 1);
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
@@ -224,7 +252,8 @@ __global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, in
 
 cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st) {
   if (a.n > 0) {
-    int grid = (int)std::min<int64_t>((a.n + 255) / 256, (int64_t)sms * 8);
+    int grid = (int)std::min<int64_t>((a.n + 256 * kHistRows - 1) / (256 * kHistRows),
+                                      (int64_t)sms * 8);
     hist_kernel<<<grid, 256, 0, st>>>(a);
   }
   scan_kernel<<<a.scan_tiles, kScanThreads, 0, st>>>(a);
