@@ -137,15 +137,14 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
     set_error(P.err, kErrInternal);
 }
 
-// one round of class c >= 1 for this warp: kw <= 32/G subsets (stack
-// entries base, base - 1, ...), G lanes each
+// one round of class c >= 1 for this warp: kw <= 32/G subsets, G lanes
+// each; rec is the record of the lane's group (read before the round)
 template <typename T, int D, bool VAR>
 __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                            int64_t gb, int c, int lane, Counters &cnt, int kw, int base) {
+                            int64_t gb, int c, int lane, Counters &cnt, int kw, uint32_t rec) {
   const int lg = c - 1, G = 1 << lg;
   const int gid = lane >> lg, gl = lane & (G - 1);
   const bool act = gid < kw;
-  const uint32_t rec = act ? S.stk(c)[base - gid] : 0u;
   const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
 
   // Steps 1-2: moments about the set's first particle
@@ -232,13 +231,12 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   __syncwarp();
 }
 
-// one round of two-particle sets for this warp: kw <= 32 of them (stack
-// entries base, base - 1, ...), one per lane
+// one round of two-particle sets for this warp: kw <= 32 of them, one per
+// lane; rec is the lane's record (read before the round)
 template <typename T, int D, bool VAR>
 __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                           int64_t gb, int lane, Counters &cnt, int kw, int base) {
+                           int64_t gb, int lane, Counters &cnt, int kw, uint32_t rec) {
   const bool act = lane < kw;
-  const uint32_t rec = act ? S.stk(0)[base - lane] : 0u;
   if (!act) return;
   const int b = rec_begin(rec), par = rec_par(rec);
   const int ja = S.idx(par)[b], jb = S.idx(par)[b + 1];
@@ -432,7 +430,9 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         }
       }
       // rounds: the team pops up to TEAM * 32/G subsets of the largest
-      // non-empty class; warp wt takes the wt-th share
+      // non-empty class; warp wt takes the wt-th share.  Each lane reads its
+      // record before the stack height drops: children pushed in this round
+      // may reuse the popped slots.
       for (;;) {
         __syncthreads();
         int c = -1;
@@ -445,14 +445,19 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         const int k = min(avail, TEAM * per);
         const int kw = max(0, min(per, k - wt * per));
         const int base = avail - 1 - wt * per;
+        uint32_t rec = 0u;
+        if (kw > 0) {
+          const int gid = c <= 1 ? lane : (lane >> (c - 1));
+          if (gid < kw) rec = S.stk(c)[base - gid];
+        }
         __syncthreads();
         if (tt == 0) S.top[c] = avail - k;
         __syncthreads();
         if (kw > 0) {
           if (c == 0)
-            pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, base);
+            pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, rec);
           else
-            group_round<T, D, VAR>(P, S, perm, gb, c, lane, cnt, kw, base);
+            group_round<T, D, VAR>(P, S, perm, gb, c, lane, cnt, kw, rec);
         }
         __syncwarp();
       }
