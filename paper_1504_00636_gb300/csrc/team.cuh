@@ -53,9 +53,13 @@ __host__ __device__ inline int class_capacity(int c, int cap) {
   return cap / lo;
 }
 
+// Pending pairs (n0) and 3-12-particle subsets (n1) are disjoint subsets of
+// the tile, so 2 n0 + 3 n1 <= cap and n0 + n1 <= cap / 2: the two classes
+// share one region of cap / 2 records, pairs from the front and the 3-12
+// class from the back.  Every other class has a region of its own.
 __host__ __device__ inline int stacks_entries(int cap) {
-  int t = 0;
-  for (int c = 0; c < kClasses; ++c) t += class_capacity(c, cap);
+  int t = cap / 2;
+  for (int c = 2; c < kClasses; ++c) t += class_capacity(c, cap);
   return t;
 }
 
@@ -75,11 +79,15 @@ struct WarpTile {
   uint16_t *idx0;  // [2][cap] index arrays, by depth parity
   uint32_t *stk0;  // the class stacks, back to back
   int *top;        // [kClasses] stack heights
-  uint16_t *soff;  // [kClasses] first entry of each stack, [kClasses] capacities
+  uint16_t *soff;  // [kClasses] first entry of each stack (class 1: the end
+                   // of the region shared with class 0), [kClasses] capacities
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
   __device__ __forceinline__ uint16_t *idx(int par) const { return idx0 + par * cap; }
-  __device__ __forceinline__ uint32_t *stk(int c) const { return stk0 + soff[c]; }
+  // entry i of class c's stack (class 1 runs backwards from its region's end)
+  __device__ __forceinline__ uint32_t *rec(int c, int i) const {
+    return c == 1 ? stk0 + (soff[1] - 1 - i) : stk0 + soff[c] + i;
+  }
   __device__ __forceinline__ int stk_cap(int c) const { return soff[kClasses + c]; }
 };
 
@@ -132,7 +140,7 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
   const int c = size_class(m);
   const int slot = atomicAdd(&S.top[c], 1);
   if (slot < S.stk_cap(c))
-    S.stk(c)[slot] = pack_rec(b, m, par);
+    *S.rec(c, slot) = pack_rec(b, m, par);
   else
     set_error(P.err, kErrInternal);
 }
@@ -313,11 +321,13 @@ __device__ __forceinline__ void unit_at(const Problem &P, const UnitSource &U, i
   }
 }
 
-// The float small-cell teams are register-limited: keep 7, 6 and 5 CTAs per
-// SM for D <= 4, 5 and 6; the other instances are limited by shared memory.
+// The float small-cell teams are register-limited: keep 7 CTAs per SM for
+// D <= 5 and 6 for D = 6 (what shared memory allows for D = 5 and 6; for
+// D <= 4 an eighth CTA would fit but its 64-register limit measured slower);
+// the other instances are limited by shared memory.
 template <typename T, int D, int TEAM>
 constexpr int team_min_blocks() {
-  return (sizeof(T) == 4 && TEAM == 4) ? (D <= 4 ? 7 : (D == 5 ? 6 : 5)) : 1;
+  return (sizeof(T) == 4 && TEAM == 4) ? (D <= 5 ? 7 : 6) : 1;
 }
 
 template <typename T, int D, int TEAM, bool VAR>
@@ -341,9 +351,9 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     S.soff = reinterpret_cast<uint16_t *>(ctl + 1);
     S.cap = cap;
     if (tt < kClasses) {
-      int o = 0;
-      for (int c = 0; c < tt; ++c) o += class_capacity(c, cap);
-      S.soff[tt] = (uint16_t)o;
+      int o = cap / 2;  // classes 0 and 1 share [0, cap / 2)
+      for (int c = 2; c < tt; ++c) o += class_capacity(c, cap);
+      S.soff[tt] = (uint16_t)(tt == 0 ? 0 : o);
       S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap);
     }
   }
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           cnt.leaves += 1;
         } else {
           const int c = size_class(n);
-          S.stk(c)[0] = pack_rec(0, n, 0);
+          *S.rec(c, 0) = pack_rec(0, n, 0);
           S.top[c] = 1;
         }
       }
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         uint32_t rec = 0u;
         if (kw > 0) {
           const int gid = c <= 1 ? lane : (lane >> (c - 1));
-          if (gid < kw) rec = S.stk(c)[base - gid];
+          if (gid < kw) rec = *S.rec(c, base - gid);
         }
         __syncthreads();
         if (tt == 0) S.top[c] = avail - k;
