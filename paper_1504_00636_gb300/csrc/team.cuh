@@ -33,6 +33,7 @@ namespace pma {
 constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
 constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
 constexpr int kMaxCapW = 8191;
+constexpr int kMaxTeam = 8;    // warps of the largest team
 
 // size class of a subset of m >= 2 particles
 __device__ __forceinline__ int size_class(int m) {
@@ -81,6 +82,7 @@ struct WarpTile {
   int *top;        // [kClasses] stack heights
   uint16_t *soff;  // [kClasses] first entry of each stack (class 1: the end
                    // of the region shared with class 0), [kClasses] capacities
+  void *wide;      // wide rounds: [kMaxTeam] partial moments, [kMaxTeam] counts
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
   __device__ __forceinline__ uint16_t *idx(int par) const { return idx0 + par * cap; }
@@ -97,6 +99,8 @@ __host__ __device__ inline size_t warp_region_bytes(int cap) {
   b = (b + 15) & ~size_t(15);
   b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 1) * sizeof(int) +
        2 * kClasses * sizeof(uint16_t);
+  b = (b + 15) & ~size_t(15);
+  b += kMaxTeam * (sizeof(Moments<T, D>) + sizeof(int));
   return (b + 15) & ~size_t(15);
 }
 
@@ -239,6 +243,121 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   __syncwarp();
 }
 
+// A wide round: the (up to TEAM/2) pending sets of 193 or more particles,
+// when they would leave warps idle, each get W = TEAM/2^k warps.
+// Moments: each warp sums a strided share, the W partial sums are merged in
+// warp order through shared memory.  Cut: warp u of the group takes the
+// u-th contiguous segment of the set (32 lanes at a time, conflict-free), a
+// first pass counts its V1 members, and a second writes V1 to the front and
+// V2 to the back of the range at the offsets of the earlier segments, which
+// is the order one warp would write.  Every warp of the team calls this
+// (the idle ones too): it contains CTA barriers.
+template <typename T, int D, bool VAR, int TEAM>
+__device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                           int64_t gb, int lane, int wt, int sub, int W, bool act, uint32_t rec,
+                           Counters &cnt) {
+  Moments<T, D> *xm = static_cast<Moments<T, D> *>(S.wide);
+  int *xc = reinterpret_cast<int *>(xm + kMaxTeam);
+  const unsigned full = 0xffffffffu;
+  const int wl = wt - sub * W;  // warp within the group
+  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
+  const uint16_t *ix = S.idx(par);
+  // Steps 1-2: moments about the set's first particle
+  T s[D];
+  {
+    const int j0 = act ? ix[b] : 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
+  }
+  Moments<T, D> M;
+  M.zero();
+#pragma unroll 4
+  for (int i = wl * 32 + lane; i < m; i += 32 * W) {
+    const int j = ix[b + i];
+    T q[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+    M.add(S.col(D)[j], q, s);
+  }
+  M.warp_allreduce();
+  if (lane == 0) xm[wt] = M;
+  __syncthreads();
+  Cut cut;
+  cut.leaf = 1;
+  cut.k = 0;
+  cut.Q = 0.0;
+  cut.Qt = 0.f;
+  if (act) {
+    Moments<T, D> Mt = xm[sub * W];
+    for (int u = 1; u < W; ++u) Mt.merge(xm[sub * W + u]);
+    cut = Decider<T, D, VAR>::run(P, Mt, s);
+  }
+  const bool split = act && !cut.leaf;
+  // Step 6: two passes over this warp's segment
+  const int np = par ^ 1;
+  const T *qk = S.col(cut.k);
+  const int seg = ((m + 32 * W - 1) / (32 * W)) * 32;
+  const int s0 = min(m, wl * seg), s1 = min(m, s0 + seg);
+  const unsigned lt = lanemask_lt();
+  int cl = 0;
+  if (split)
+    for (int i0 = s0; i0 < s1; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < s1;
+      const bool lft = valid && Decider<T, D, VAR>::left(qk[ix[b + (valid ? i : 0)]], cut);
+      cl += __popc(__ballot_sync(full, lft));
+    }
+  if (lane == 0) xc[wt] = cl;
+  __syncthreads();
+  int rl = 0, rr = 0, totL = 0;
+  for (int u = 0; u < W; ++u) {
+    const int cu = act ? xc[sub * W + u] : 0;
+    const int nu = min(m, (u + 1) * seg) - min(m, u * seg);
+    if (u < wl) {
+      rl += cu;
+      rr += nu - cu;
+    }
+    totL += cu;
+  }
+  if (split) {
+    uint16_t *ox = S.idx(np);
+    for (int i0 = s0; i0 < s1; i0 += 32) {
+      const int i = i0 + lane;
+      const bool valid = i < s1;
+      const int j = valid ? ix[b + i] : 0;
+      const bool lft = valid && Decider<T, D, VAR>::left(qk[j], cut);
+      const unsigned bl = __ballot_sync(full, lft);
+      const unsigned br = __ballot_sync(full, valid && !lft);
+      if (valid) {
+        const int dst = lft ? (b + rl + __popc(bl & lt)) : (b + m - 1 - rr - __popc(br & lt));
+        ox[dst] = (uint16_t)j;
+      }
+      rl += __popc(bl);
+      rr += __popc(br);
+    }
+  }
+  __syncthreads();
+  const bool degenerate = split && (totL == 0 || totL == m);
+  const bool final_set = act && (cut.leaf || degenerate);
+  if (final_set) {
+    const uint16_t *fx = S.idx(cut.leaf ? par : np);
+    const int h = head_code(m);
+    for (int i = wl * 32 + lane; i < m; i += 32 * W)
+      mark_final<T, D>(S, b + i, fx[b + i], i == 0 ? h : 0);
+  }
+  if (act && wl == 0 && lane == 0) {
+    if (final_set) {
+      cnt.leaves += 1;
+      if (degenerate) cnt.degenerate += 1;
+    } else {
+      cnt.splits += 1;
+      cnt.depth += (unsigned long long)m;
+      push_child<T, D>(P, S, perm, gb, b, totL, np, cnt);
+      push_child<T, D>(P, S, perm, gb, b + totL, m - totL, np, cnt);
+    }
+  }
+}
+
 // one round of two-particle sets for this warp: kw <= 32 of them, one per
 // lane; rec is the lane's record (read before the round)
 template <typename T, int D, bool VAR>
@@ -349,6 +468,12 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     S.top = reinterpret_cast<int *>(S.stk0 + stacks_entries(cap));
     ctl = S.top + kClasses;
     S.soff = reinterpret_cast<uint16_t *>(ctl + 1);
+    {
+      const size_t woff =
+          ((size_t)(reinterpret_cast<unsigned char *>(S.soff + 2 * kClasses) - base) + 15) &
+          ~size_t(15);
+      S.wide = base + woff;
+    }
     S.cap = cap;
     if (tt < kClasses) {
       int o = cap / 2;  // classes 0 and 1 share [0, cap / 2)
@@ -450,8 +575,24 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         for (int k = kClasses - 1; k >= 0; --k)
           if (c < 0 && S.top[k] > 0) c = k;
         if (c < 0) break;
-        const int per = (c == 0) ? 32 : (32 >> (c - 1));
         const int avail = S.top[c];
+        if (TEAM == kMaxTeam && c == kClasses - 1 && avail * 2 <= TEAM) {
+          // few large sets: several warps per set (wide round).  Only the
+          // 8-warp teams (one or two CTAs per SM) use it: in the 4-warp teams
+          // other CTAs fill the idle warps' issue slots, and the extra
+          // barriers measured slower.
+          int W = TEAM;
+          while (W * avail > TEAM) W >>= 1;
+          const int sub = wt / W;
+          const bool act = sub < avail;
+          const uint32_t rec = act ? *S.rec(c, avail - 1 - sub) : 0u;
+          __syncthreads();
+          if (tt == 0) S.top[c] = 0;
+          __syncthreads();
+          wide_round<T, D, VAR, TEAM>(P, S, perm, gb, lane, wt, sub, W, act, rec, cnt);
+          continue;
+        }
+        const int per = (c == 0) ? 32 : (32 >> (c - 1));
         const int k = min(avail, TEAM * per);
         const int kw = max(0, min(per, k - wt * per));
         const int base = avail - 1 - wt * per;
