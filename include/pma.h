@@ -182,7 +182,7 @@ int pma_get_stats(const pma_handle *h, pma_stats *out);
  * completed) writes up to n durations in milliseconds, averaged over the
  * calls since timing was enabled (the last 64 of them):
  *   [0] Step 1 binning        [1] big-cell cuts (global memory)
- *   [2] warp-per-cell cells   [3] CTA-per-cell cells   [4] big-cell pieces
+ *   [2] small-cell teams      [3] large-cell teams      [4] big-cell pieces
  *   [5] Step 7 emit           [6] whole call
  * and returns PMA_ERR_INVALID_ARG when timing is off or nothing was timed.
  */

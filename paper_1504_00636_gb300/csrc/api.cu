@@ -7,9 +7,10 @@
 //   radix prep / passes     Step 1 for ungrouped input: stable sort by cell
 //   big_kernel              cells too large for shared memory: top cuts in
 //                           global memory until every piece fits
-//   unit_kernel (cells)     Steps 2-6 per cell in shared memory
-//   unit_kernel (pieces)    Steps 2-6 on the pieces of big cells
-//   emit_kernel             Step 7: centroids, compacted, canonical order
+//   team_kernel (3 launches) Steps 2-6 in shared memory: cells of up to
+//                           1024 particles (4-warp teams), larger cells and
+//                           the pieces of big cells (8-warp teams)
+//   count / tiles / emit    Step 7: centroids, compacted, canonical order
 // and a 1-line status copy (count, error bits, counters) to pinned memory.
 #include <algorithm>
 #include <cmath>
