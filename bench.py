@@ -166,6 +166,27 @@ def ncu_traffic(kernel, workload_name, precision):
         return None
 
 
+# ----------------------------------------------------------- multi-rank
+
+def max_over_ranks(t_ms, world, device=None):
+    """This rank's timed milliseconds, or their maximum over the ranks of the
+    job (one process per GPU, each merging its own replica)."""
+    t = float(t_ms)
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def job_throughput(n_per_rank, steps, world, t_ms):
+    """Whole-job Mparticles/s: every rank merges n_per_rank particles per step
+    (weak scaling), and the job takes the slowest rank's time."""
+    return world * n_per_rank * steps / (t_ms * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------- runs
 
 def to_device(p, mixed, dev):
@@ -459,19 +480,13 @@ def main():
     clk = clocks.stop()
 
     def agg(ms_list):
-        t = float(np.sum(ms_list))
-        if world > 1:
-            import torch.distributed as dist
-            x = torch.tensor([t], device=dev)
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            t = float(x.item())
-        return t
+        return max_over_ranks(np.sum(ms_list), world, dev)
 
     lines = {}
     for mixed, res in results.items():
         q = p.astype(np.float32) if mixed else p
         t_ms = agg(res["ms"])
-        v = world * p.n * args.steps / (t_ms * 1e-3) / 1e6
+        v = job_throughput(p.n, args.steps, world, t_ms)
         b_in, b_out = bytes_per_particle(q, mixed)
         step_bytes = p.n * (b_in + 4) + res["M"] * b_out
         lines[mixed] = dict(
@@ -483,10 +498,19 @@ def main():
             depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"],
             graph=res["graph"],
             eager_ms_per_step=round(float(np.mean(res["eager_ms"])), 4))
-    if rank != 0:
-        return
     head = lines[True] if True in lines else lines[False]
     mixed_head = True in lines
+    e2e = None
+    if not args.no_e2e:
+        # every rank copies its own replica in and out; the job takes the
+        # slowest rank's time
+        q = p.astype(np.float32) if mixed_head else p
+        e = time_e2e(q, mixed_head, max(3, args.steps // 4), 2)
+        t_e2e = max_over_ranks(1e3 * float(np.mean(e["s"])), world, dev)
+        e2e = {"value": round(job_throughput(p.n, 1, world, t_e2e), 2), "unit": UNIT,
+               "h2d_bytes_per_step": e["h2d"] * world, "d2h_bytes_per_step": e["d2h"] * world}
+    if rank != 0:
+        return
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -502,12 +526,8 @@ def main():
                               "cuda_graph": f["graph"], "eager_ms_per_step": f["eager_ms_per_step"],
                               "roofline": f["roofline"], "stage_ms": f["stage_ms"], "M": f["M"],
                               "speedup_mixed_over_fp64": round(head["value"] / f["value"], 3)}
-    if not args.no_e2e:
-        q = p.astype(np.float32) if mixed_head else p
-        e = time_e2e(q, mixed_head, max(3, args.steps // 4), 2)
-        ev = p.n / float(np.mean(e["s"])) / 1e6
-        line["e2e"] = {"value": round(ev, 2), "unit": UNIT, "h2d_bytes_per_step": e["h2d"],
-                       "d2h_bytes_per_step": e["d2h"]}
+    if e2e is not None:
+        line["e2e"] = e2e
     if mixed_head and not args.no_accuracy:
         line["accuracy_mixed"] = accuracy_report(p, dev)
     if not args.no_cpu:
