@@ -272,6 +272,54 @@ def test_async_merge_then_sync_and_host_variant():
     m.close()
 
 
+def _host_call(p, precision):
+    """pma_merge_host on numpy arrays: returns M, outputs, counters."""
+    mixed = precision == "mixed"
+    ft = np.float32 if mixed else np.float64
+    m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min, precision)
+    N = p.n
+    hc, hw, hi = np.empty(N, np.int32), np.empty(N), np.empty(N, np.int32)
+    hp = [np.empty(N, ft) for _ in range(p.dx)]
+    hm = [np.empty(N) for _ in range(p.dp)]
+    o = binding.pma_output()
+    o.cell, o.w, o.index = hc.ctypes.data, hw.ctypes.data, hi.ctypes.data
+    for a in range(p.dx):
+        o.pos[a] = hp[a].ctypes.data
+    for a in range(p.dp):
+        o.mom[a] = hm[a].ctypes.data
+    pc = [np.ascontiguousarray(p.pos[a], ft) for a in range(p.dx)]
+    mc = [np.ascontiguousarray(p.mom[a], ft) for a in range(p.dp)]
+    wc = np.ascontiguousarray(p.w, ft)
+    M = binding.pma_merge_host(m.handle, N, p.cell.ctypes.data, [x.ctypes.data for x in pc],
+                               [x.ctypes.data for x in mc], wc.ctypes.data, p.tol_x, p.tol_p, o)
+    st = m.stats()
+    m.close()
+    return M, dict(cell=hc[:M], pos=np.stack([x[:M] for x in hp]), mom=np.stack([x[:M] for x in hm]),
+                   w=hw[:M], index=hi), st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shuffle", [False, True], ids=["grouped", "shuffled"])
+def test_host_call_equals_device_call(precision, shuffle):
+    # the host-buffer call on 2.6M particles (grouped or not) gives the
+    # device call's result bit for bit
+    p = synth.two_stream(cells=2600)
+    if shuffle:
+        p = p.shuffled(9)
+    if precision == "mixed":
+        p = p.astype(np.float32)
+    g = run_gpu(p, precision)
+    M, h, st = _host_call(p, precision)
+    assert M == g["count"]
+    for key in ("cell", "w", "index"):
+        np.testing.assert_array_equal(h[key], g[key])
+    np.testing.assert_array_equal(h["mom"], g["mom"])
+    np.testing.assert_array_equal(h["pos"].astype(np.float64), g["pos"])
+    for key in ("splits", "leaves", "depth_sum", "cells_merged"):
+        assert st[key] == g["stats"][key]
+    assert st["n_out"] == M and st["sorted_input"] == (0 if shuffle else 1)
+
+
 @pytest.mark.parametrize("bad", ["cell", "weight", "nan"])
 def test_bad_particle_data_is_reported(bad):
     p = synth.counter_beams(cells=4)
@@ -353,3 +401,12 @@ def test_merge_step_replays_from_a_cuda_graph():
         assert torch.equal(out.index, ref.index)
         assert torch.equal(out.w[:ref_M], ref.w[:ref_M])
     m.close()
+
+
+def test_host_call_reports_bad_data():
+    # a bad weight near the end of a 2.6M-particle host call is reported
+    p = synth.two_stream(cells=2600)
+    p.w[p.n - 10] = -1.0
+    with pytest.raises(binding.PmaError) as ei:
+        _host_call(p, "fp64")
+    assert ei.value.code == binding.PMA_ERR_INPUT
