@@ -35,6 +35,8 @@ struct Ctl {
   int32_t unit_next[2];
   int32_t warp_count;
   int32_t warp_next;
+  int32_t tiny_count;
+  int32_t tiny_next;
   int32_t block_count;
   int32_t bin_ticket;
   int32_t emit_ticket;
@@ -69,6 +71,8 @@ struct pma_handle {
   int cap = 0;
   int unit_grid = 0;
   int cap_w = 0;
+  int cap_t = 0;
+  int tiny_grid = 0;
   int warp_grid = 0;
   int64_t capacity = 0;
   int bin_tiles = 0;
@@ -78,7 +82,7 @@ struct pma_handle {
   int32_t *counts = nullptr, *cell_begin = nullptr, *radix_count = nullptr;
   unsigned long long *radix_status = nullptr;
   int32_t *perm = nullptr, *perm_tmp = nullptr, *perm_final = nullptr, *big_list = nullptr;
-  int32_t *warp_list = nullptr, *block_list = nullptr;
+  int32_t *warp_list = nullptr, *block_list = nullptr, *tiny_list = nullptr;
   void *fin = nullptr;  // staging: D + 1 columns of fin_stride entries
   int64_t fin_stride = 0;  // capacity rounded up to 16 entries (bulk-copy alignment)
   uint8_t *head = nullptr;
@@ -125,7 +129,7 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->radix_count, h->radix_status, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->bin_status, h->tile_count, h->tile_prefix,
-                  h->pieces, h->ctl, h->warp_list, h->block_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
+                  h->pieces, h->ctl, h->warp_list, h->block_list, h->tiny_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -243,6 +247,12 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   while (h->cap_w > 128 && team_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
     h->cap_w -= 64;
   h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, h->cap_w) + 1024)));
+  // tiny cells (up to 256 particles) go to one-warp teams with a small tile:
+  // many cells in flight per SM, and no warp of a team waits for another
+  h->cap_t = 256;
+  // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
+  h->tiny_grid =
+      h->sms * std::min<int>(24, std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, h->cap_t) + 1024))));
   int cap = 8191;
   while (cap > h->cap_w && team_smem(h->mixed, h->D, cap) > (size_t)smem_optin) cap -= 64;
   h->cap = cap;
@@ -260,6 +270,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, Npad) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
+            dalloc(&h->tiny_list, C) == cudaSuccess &&
             cudaMalloc(&h->fin, (size_t)Npad * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->tile_count, h->emit_tiles_max) == cudaSuccess &&
@@ -349,6 +360,9 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   b.cap_w = h->cap_w;
   b.warp_list = h->warp_list;
   b.warp_count = &h->ctl->warp_count;
+  b.cap_t = h->cap_t;
+  b.tiny_list = h->tiny_list;
+  b.tiny_count = &h->ctl->tiny_count;
   b.block_list = h->block_list;
   b.block_count = &h->ctl->block_count;
   b.err = &h->ctl->err;
@@ -420,12 +434,18 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.warp_list = h->warp_list;
   P.warp_count = &h->ctl->warp_count;
   P.warp_next = &h->ctl->warp_next;
+  P.cap_t = h->cap_t;
+  P.tiny_list = h->tiny_list;
+  P.tiny_count = &h->ctl->tiny_count;
+  P.tiny_next = &h->ctl->tiny_next;
   P.block_list = h->block_list;
   P.block_count = &h->ctl->block_count;
 
   e = launch_big(P, h->mixed, h->sms, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);
+  e = launch_team(P, h->mixed, 3, 1, h->cap_t, h->tiny_grid, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "team launch (tiny cells)");
   e = launch_team(P, h->mixed, 0, 4, h->cap_w, h->warp_grid, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (small cells)");
   mark(h, 3, st);

@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
     sum += v[j];
     if (v[j] > 0) {
       // population class of the cell
-      if (v[j] <= a.n_min || v[j] <= a.cap_w)
+      if (v[j] <= a.cap_t)
+        a.tiny_list[atomicAdd(a.tiny_count, 1)] = (int)i;
+      else if (v[j] <= a.n_min || v[j] <= a.cap_w)
         a.warp_list[atomicAdd(a.warp_count, 1)] = (int)i;
       else if (v[j] <= a.cap)
         a.block_list[atomicAdd(a.block_count, 1)] = (int)i;

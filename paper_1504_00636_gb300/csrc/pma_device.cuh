@@ -91,6 +91,11 @@ struct Problem {
   int32_t *warp_list;
   int32_t *warp_count;
   int32_t *warp_next;
+  // tiny cells (at most cap_t particles) go to one-warp teams
+  int32_t cap_t;
+  int32_t *tiny_list;
+  int32_t *tiny_count;
+  int32_t *tiny_next;
   int32_t *block_list;
   int32_t *block_count;
 };

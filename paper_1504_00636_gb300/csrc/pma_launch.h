@@ -33,6 +33,9 @@ struct BinArgs {
   int32_t cap_w;
   int32_t *warp_list;
   int32_t *warp_count;
+  int32_t cap_t;          // cells of at most cap_t particles: the tiny class
+  int32_t *tiny_list;
+  int32_t *tiny_count;
   int32_t *block_list;
   int32_t *block_count;
   unsigned *err;

@@ -414,9 +414,10 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
 
 // --------------------------------------------------------------- kernel
 
-// Work sources: mode 0 the cells of the small class (and pass-through
-// cells), mode 1 the cells of the large class, mode 2 the pieces of cells
-// that were first cut in global memory.
+// Work sources: mode 3 the cells of the tiny class (one-warp teams), mode 0
+// the cells of the small class (and larger pass-through cells), mode 1 the
+// cells of the large class, mode 2 the pieces of cells that were first cut
+// in global memory.
 struct UnitSource {
   const int32_t *list;
   const int32_t *count;
@@ -453,6 +454,8 @@ template <typename T, int D, int TEAM, bool VAR>
 __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     team_kernel(Problem P, UnitSource U, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int count = *U.count;
+  if (count == 0) return;  // an empty class: leave before any other work
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, tt = threadIdx.x;
   constexpr int kThreads = 32 * TEAM;
   WarpTile<T, D> S;
@@ -483,13 +486,16 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     }
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
-  const int count = *U.count;
-  const int chunk = U.mode == 0 ? kWarpChunk : 1;
+  const int chunk = (U.mode == 0 || U.mode == 3) ? kWarpChunk : 1;
   Counters cnt{0ull, 0ull, 0ull, 0ull};
   unsigned long long merged = 0, passed = 0;
 
   for (;;) {
-    if (tt == 0) ctl[0] = atomicAdd(U.next, chunk);
+    if (tt == 0) {
+      // once the counter has passed the end, stop without another atomic
+      const int seen = *reinterpret_cast<volatile int *>(U.next);
+      ctl[0] = seen >= count ? seen : atomicAdd(U.next, chunk);
+    }
     __syncthreads();
     const int c0 = ctl[0];
     __syncthreads();
@@ -696,6 +702,9 @@ static cudaError_t launch_team_d(const Problem &P, const UnitSource &U, int cap,
 template <bool VAR>
 static cudaError_t launch_team_build(const Problem &P, const UnitSource &U, int mixed,
                                      int team, int cap, int grid, cudaStream_t st) {
+  if (team == 1)
+    return mixed ? launch_team_d<float, 1, VAR>(P, U, cap, grid, st)
+                 : launch_team_d<double, 1, VAR>(P, U, cap, grid, st);
   if (team == 4)
     return mixed ? launch_team_d<float, 4, VAR>(P, U, cap, grid, st)
                  : launch_team_d<double, 4, VAR>(P, U, cap, grid, st);

@@ -18,6 +18,10 @@ cudaError_t launch_team(const Problem &P, int mixed, int mode, int team, int cap
     U.list = P.warp_list;
     U.count = P.warp_count;
     U.next = P.warp_next;
+  } else if (mode == 3) {
+    U.list = P.tiny_list;
+    U.count = P.tiny_count;
+    U.next = P.tiny_next;
   } else if (mode == 1) {
     U.list = P.block_list;
     U.count = P.block_count;
