@@ -64,7 +64,7 @@ extern "C" {
  *       vector: Delta_l = sigma_l / |P|, |P| = sqrt(sum over momentum axes
  *       of P_l^2), instead of sigma_l / |P_l|.  Sets whose mean momentum is
  *       near zero on one axis then stop splitting on that axis.
- * They apply to pma_merge and pma_merge_host; pma_merge_noalloc ignores them.
+ * They apply to pma_merge and pma_merge_host; pma_merge_noalloc refuses them.
  */
 #define PMA_FLAG_SPLIT_NORMALIZED 2u
 #define PMA_FLAG_MOMENTUM_NORM 4u
@@ -100,6 +100,29 @@ typedef struct pma_config {
 } pma_config;
 
 /*
+ * Near-tie bits of a cell (pma_output.cell_flags).  In exact arithmetic the
+ * partition of Steps 2-6 is unique; in floating point a decision taken
+ * within rounding of the opposite outcome may differ between two correct
+ * implementations.  A cell carries:
+ *   PMA_NEAR_STOP    some Delta_l within about 1e-9 (relative) of its
+ *                    tolerance in a Step 3 stop test
+ *   PMA_NEAR_ARGMAX  the runner-up axis of a Step 4 choice within about 1e-9
+ *                    (relative) of the chosen one
+ *   PMA_NEAR_CUT     a particle within 64 m eps (|s_k| + sigma_k) of the
+ *                    Step 5 cut value Q_k of a set of m particles
+ *   PMA_RECHECKED    (PMA_MIXED) an FP32 decision or cut closer than its
+ *                    error bound was taken again in FP64 from the particles;
+ *                    informational, the result is the FP64 decision
+ * With PMA_MIXED every decision is certified: an FP32 comparison is used
+ * only when its error bound shows it equals the exact one, so a cell without
+ * PMA_NEAR_* bits has the exact-arithmetic partition of its stored values.
+ */
+#define PMA_NEAR_STOP 1u
+#define PMA_NEAR_ARGMAX 2u
+#define PMA_NEAR_CUT 4u
+#define PMA_RECHECKED 8u
+
+/*
  * Caller-owned device output buffers; every array has room for `capacity`
  * entries (the output count M never exceeds the input count n).
  *   cell[M]           int32 cell id of each merged particle
@@ -108,6 +131,9 @@ typedef struct pma_config {
  *   w[M]              FP64 centroid weight
  *   index[n]          int32: output slot of every input particle, or NULL
  *   count_dev         int64 device word receiving M, or NULL
+ *   cell_flags[n_cells]  uint32 PMA_NEAR_* / PMA_RECHECKED bits of every
+ *                     cell, or NULL (pma_merge only; the other entry points
+ *                     ignore it)
  */
 typedef struct pma_output {
     int32_t *cell;
@@ -116,6 +142,7 @@ typedef struct pma_output {
     double *w;
     int32_t *index;
     int64_t *count_dev;
+    uint32_t *cell_flags;
 } pma_output;
 
 /* Per-call counters (filled after a synchronous call). */
@@ -130,6 +157,14 @@ typedef struct pma_stats {
     int64_t degenerate_cuts;   /* cuts whose rounded centroid left a side empty */
     int64_t big_cells;         /* cells too large for one CTA's shared memory */
     int64_t sorted_input;      /* 1 if the cell ids were already non-decreasing */
+    int64_t near_stop;         /* decisions flagged PMA_NEAR_STOP */
+    int64_t near_argmax;       /* decisions flagged PMA_NEAR_ARGMAX */
+    int64_t near_cut;          /* cuts flagged PMA_NEAR_CUT */
+    int64_t fp64_rechecks;     /* PMA_MIXED: FP32 decisions taken again in FP64 */
+    int64_t cells_flagged;     /* cells with at least one PMA_NEAR_* / PMA_RECHECKED bit */
+    int64_t cells_tiny;        /* cells per population path: up to 256 particles */
+    int64_t cells_small;       /*   up to the small-class tile (and pass-through) */
+    int64_t cells_large;       /*   up to one CTA's shared memory; big_cells above */
 } pma_stats;
 
 /*
@@ -170,6 +205,34 @@ int pma_merge_host(pma_handle *h, int64_t n, const int32_t *cells,
                    const void *weights, double tol_x, double tol_p,
                    const pma_output *out_host, int64_t *count_host, void *stream);
 
+/*
+ * Bounded device waits.  The single-pass prefix scans (Step 1 binning and
+ * Step 7 output slots) let a CTA wait for the status word of the CTA before
+ * it.  Every such wait gives up after `wait_ns` nanoseconds (default 2 s; 0
+ * restores it; otherwise >= 1000): the kernel then sets an error bit and
+ * returns, the kernels after it in the call return at once, and the call
+ * reports PMA_ERR_TIMEOUT.  The device context stays usable and the next
+ * call starts afresh.  (No counterpart in the paper: a safeguard of this
+ * implementation.)
+ */
+int pma_set_wait_limit(pma_handle *h, int64_t wait_ns);
+
+/*
+ * Failure-detection test hook (not for production use; no counterpart in
+ * the paper): while `tile` >= 0, every call's Step 1 prefix scan withholds
+ * the status word of that scan tile (a tile covers 2048 cells), so that the
+ * tile after it waits out its limit and the call returns PMA_ERR_TIMEOUT
+ * without faulting or hanging the device.  tile < 0 turns the hook off.
+ */
+int pma_test_withhold_status(pma_handle *h, int tile);
+
+/*
+ * Failure-detection test hook: the status a call reports for a device error
+ * word with these bits (1 bad particle data, 4 a bounded wait gave up, 2 an
+ * internal bound; the first of these in that order wins, 0 is PMA_OK).
+ */
+int pma_test_status_of_bits(unsigned bits);
+
 /* Wait for the handle's last enqueued call and return its device status. */
 int pma_sync(pma_handle *h);
 
@@ -200,7 +263,9 @@ int pma_get_timing(const pma_handle *h, float *ms, int n);
  * 1 MB, held by every GPU that loads the library until the process exits),
  * and the caller passes only inputs and outputs.
  *   cfg          dx, dp, cell_size, n_cells, n_min and precision as for
- *                pma_create (capacity and flags are ignored)
+ *                pma_create; capacity is ignored; flags may hold only
+ *                PMA_FLAG_NO_INDEX (the paper's rule and plain Step 7 only:
+ *                any other flag returns PMA_ERR_INVALID_ARG)
  *   n, cells, pos, mom, weights, tol_x, tol_p   as for pma_merge; the cell
  *                ids must be non-decreasing (particles grouped by cell)
  *   out          caller-owned device outputs as for pma_merge
@@ -211,12 +276,13 @@ int pma_get_timing(const pma_handle *h, float *ms, int n);
  * for D <= 4), else the call returns PMA_ERR_CAPACITY after the device work.
  * Unsorted or out-of-range cell ids and bad particle values return
  * PMA_ERR_INPUT.
- * The call waits for `stream` and returns the device status.  The first
- * call on each device looks up the scratch array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one scratch array, which keeps the last
- * call's contents (the part that must start at zero is cleared by every
- * call): calls that overlap on the GPU, from several streams or host
+ * The call waits for `stream` (it synchronises and copies its status to the
+ * host) and returns the device status: it must never be called while its
+ * stream is being captured into a CUDA graph.  The first call on each device
+ * also looks up the scratch array's device address (once per device, with
+ * that device current).  All calls share the one scratch array, which keeps
+ * the last call's contents (the part that must start at zero is cleared by
+ * every call): calls that overlap on the GPU, from several streams or host
  * threads, race and give wrong results.
  */
 #define PMA_NOALLOC_MAX_N 65536

@@ -30,10 +30,16 @@ PMA_FLAG_NO_INDEX = 1
 PMA_FLAG_SPLIT_NORMALIZED = 2
 PMA_FLAG_MOMENTUM_NORM = 4
 PMA_FLAG_CONSERVE_ENERGY = 8
+PMA_NEAR_STOP = 1
+PMA_NEAR_ARGMAX = 2
+PMA_NEAR_CUT = 4
+PMA_RECHECKED = 8
+PMA_NEAR_ANY = PMA_NEAR_STOP | PMA_NEAR_ARGMAX | PMA_NEAR_CUT
 
 SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
            "pma_set_timing", "pma_get_timing", "pma_merge_noalloc", "pma_destroy",
-           "pma_error_string", "pma_last_error")
+           "pma_error_string", "pma_last_error", "pma_set_wait_limit",
+           "pma_test_withhold_status", "pma_test_status_of_bits")
 PMA_NOALLOC_MAX_N = 65536
 PMA_NOALLOC_MAX_CELLS = 65536
 PMA_N_STAGES = 7
@@ -50,13 +56,16 @@ class pma_config(ctypes.Structure):
 class pma_output(ctypes.Structure):
     _fields_ = [("cell", ctypes.c_void_p), ("pos", ctypes.c_void_p * 3),
                 ("mom", ctypes.c_void_p * 3), ("w", ctypes.c_void_p),
-                ("index", ctypes.c_void_p), ("count_dev", ctypes.c_void_p)]
+                ("index", ctypes.c_void_p), ("count_dev", ctypes.c_void_p),
+                ("cell_flags", ctypes.c_void_p)]
 
 
 class pma_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n_in", "n_out", "cells_merged", "cells_passthrough", "splits", "leaves",
-        "depth_sum", "degenerate_cuts", "big_cells", "sorted_input")]
+        "depth_sum", "degenerate_cuts", "big_cells", "sorted_input", "near_stop",
+        "near_argmax", "near_cut", "fp64_rechecks", "cells_flagged", "cells_tiny",
+        "cells_small", "cells_large")]
 
 
 class PmaError(RuntimeError):
@@ -103,6 +112,12 @@ def load(build_if_missing: bool = True):
             lib.pma_get_timing.restype = ctypes.c_int
             lib.pma_merge_noalloc.argtypes = [ctypes.POINTER(pma_config)] + args[1:]
             lib.pma_merge_noalloc.restype = ctypes.c_int
+            lib.pma_set_wait_limit.argtypes = [P, ctypes.c_int64]
+            lib.pma_set_wait_limit.restype = ctypes.c_int
+            lib.pma_test_withhold_status.argtypes = [P, ctypes.c_int]
+            lib.pma_test_withhold_status.restype = ctypes.c_int
+            lib.pma_test_status_of_bits.argtypes = [ctypes.c_uint]
+            lib.pma_test_status_of_bits.restype = ctypes.c_int
             lib.pma_destroy.argtypes = [P]
             lib.pma_destroy.restype = ctypes.c_int
             lib.pma_error_string.argtypes = [ctypes.c_int]
@@ -183,6 +198,14 @@ def pma_sync(handle) -> None:
     _check(load().pma_sync(handle), handle)
 
 
+def pma_set_wait_limit(handle, wait_ns: int) -> None:
+    _check(load().pma_set_wait_limit(handle, int(wait_ns)), handle)
+
+
+def pma_test_withhold_status(handle, tile: int) -> None:
+    _check(load().pma_test_withhold_status(handle, int(tile)), handle)
+
+
 def pma_get_stats(handle) -> dict:
     s = pma_stats()
     _check(load().pma_get_stats(handle, ctypes.byref(s)), handle)
@@ -210,6 +233,7 @@ class Output:
     w: "object"
     index: "object"
     count_dev: "object"
+    cell_flags: "object" = None
 
     def struct(self) -> pma_output:
         o = pma_output()
@@ -221,6 +245,7 @@ class Output:
         o.w = self.w.data_ptr()
         o.index = self.index.data_ptr() if self.index is not None else None
         o.count_dev = self.count_dev.data_ptr() if self.count_dev is not None else None
+        o.cell_flags = self.cell_flags.data_ptr() if self.cell_flags is not None else None
         return o
 
 
@@ -264,7 +289,8 @@ class Merger:
                       [t.empty(N, dtype=t.float64, device=device) for _ in range(self.dp)],
                       t.empty(N, dtype=t.float64, device=device),
                       t.empty(N, dtype=t.int32, device=device) if index else None,
-                      t.zeros(1, dtype=t.int64, device=device))
+                      t.zeros(1, dtype=t.int64, device=device),
+                      t.zeros(self.n_cells, dtype=t.int32, device=device))
 
     def merge(self, cells, pos, mom, w, tol_x, tol_p, out: Output = None, sync=True,
               stream=None):

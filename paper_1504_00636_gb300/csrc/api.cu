@@ -19,6 +19,7 @@
 #include <new>
 #include <string>
 
+#include "lookback.cuh"
 #include "pma.h"
 #include "pma_launch.h"
 
@@ -86,6 +87,7 @@ struct pma_handle {
   void *fin = nullptr;  // staging: D + 1 columns of fin_stride entries
   int64_t fin_stride = 0;  // capacity rounded up to 16 entries (bulk-copy alignment)
   uint8_t *head = nullptr;
+  uint32_t *cell_flags = nullptr;  // near-tie bits per cell when the caller gives none
   unsigned long long *bin_status = nullptr;
   int32_t *tile_count = nullptr;
   long long *tile_prefix = nullptr;
@@ -97,6 +99,8 @@ struct pma_handle {
   Staging stage;
   bool timing = false;
   int timed = 0;     // calls recorded since timing was enabled
+  unsigned long long wait_ns = 0;  // limit of the bounded device waits (0: default)
+  int withhold_tile = -1;          // failure-detection test hook (see pma.h)
   cudaEvent_t ev[kRing][PMA_N_STAGES] = {};  // PMA_N_STAGES events per call
   cudaEvent_t *cur_ev = nullptr;
   std::string last_error;
@@ -129,7 +133,8 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->radix_count, h->radix_status, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->bin_status, h->tile_count, h->tile_prefix,
-                  h->pieces, h->ctl, h->warp_list, h->block_list, h->tiny_list, h->fin, h->stage.cells, h->stage.w, h->stage.out_cell,
+                  h->pieces, h->ctl, h->warp_list, h->block_list, h->tiny_list, h->fin, h->cell_flags,
+                  h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -151,6 +156,15 @@ void mark(pma_handle *h, int i, cudaStream_t st) {
   if (h->timing && h->cur_ev) cudaEventRecord(h->cur_ev[i], st);
 }
 
+// status code of a device error word: bad particle data first, then a wait
+// that gave up, then an internal bound
+int status_of_bits(unsigned err) {
+  if (err & kErrInput) return PMA_ERR_INPUT;
+  if (err & kErrTimeout) return PMA_ERR_TIMEOUT;
+  if (err & kErrInternal) return PMA_ERR_INTERNAL;
+  return PMA_OK;
+}
+
 int status_from_ctl(pma_handle *h) {
   const Ctl &c = *h->ctl_host;
   pma_stats &s = h->stats;
@@ -163,30 +177,41 @@ int status_from_ctl(pma_handle *h) {
   s.degenerate_cuts = (int64_t)c.stats[kStDegenerate];
   s.big_cells = (int64_t)c.stats[kStBig];
   s.sorted_input = c.unsorted ? 0 : 1;
-  if (c.err & kErrInput)
-    return fail(h, PMA_ERR_INPUT,
-                "invalid particle data (cell id out of range, w <= 0 or non-finite value)");
-  if (c.err & kErrTimeout) return fail(h, PMA_ERR_TIMEOUT, "a bounded device wait gave up");
-  if (c.err & kErrInternal)
-    return fail(h, PMA_ERR_INTERNAL, "an internal device bound was exceeded");
-  return PMA_OK;
+  s.near_stop = (int64_t)c.stats[kStNearStop];
+  s.near_argmax = (int64_t)c.stats[kStNearArgmax];
+  s.near_cut = (int64_t)c.stats[kStNearCut];
+  s.fp64_rechecks = (int64_t)c.stats[kStRecheck];
+  s.cells_flagged = (int64_t)c.stats[kStCellsFlagged];
+  s.cells_tiny = c.tiny_count;
+  s.cells_small = c.warp_count;
+  s.cells_large = c.block_count;
+  switch (status_of_bits(c.err)) {
+    case PMA_ERR_INPUT:
+      return fail(h, PMA_ERR_INPUT,
+                  "invalid particle data (cell id out of range, w <= 0 or non-finite value)");
+    case PMA_ERR_TIMEOUT: return fail(h, PMA_ERR_TIMEOUT, "a bounded device wait gave up");
+    case PMA_ERR_INTERNAL:
+      return fail(h, PMA_ERR_INTERNAL, "an internal device bound was exceeded");
+    default: return PMA_OK;
+  }
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
 
 // The regions a call must clear, zeroed by one kernel on the call's stream
-// instead of four memset calls.  Every region is a whole number of 4-byte
-// words.
+// instead of one memset per region.  Every region is a whole number of
+// 4-byte words.
+constexpr int kZeroRegions = 5;
 struct ZeroArgs {
-  uint32_t *p[4];
-  int64_t words[4];
+  uint32_t *p[kZeroRegions];
+  int64_t words[kZeroRegions];
 };
 
 __global__ void zero_kernel(ZeroArgs z) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < kZeroRegions; ++r)
     for (int64_t i = t; i < z.words[r]; i += stride) z.p[r][i] = 0u;
 }
 
@@ -270,7 +295,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->perm_tmp, N) == cudaSuccess && dalloc(&h->perm_final, Npad) == cudaSuccess &&
             dalloc(&h->big_list, C) == cudaSuccess && dalloc(&h->head, Npad) == cudaSuccess &&
             dalloc(&h->warp_list, C) == cudaSuccess && dalloc(&h->block_list, C) == cudaSuccess &&
-            dalloc(&h->tiny_list, C) == cudaSuccess &&
+            dalloc(&h->tiny_list, C) == cudaSuccess && dalloc(&h->cell_flags, C) == cudaSuccess &&
             cudaMalloc(&h->fin, (size_t)Npad * (h->D + 1) * (h->mixed ? 4 : 8)) == cudaSuccess &&
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->tile_count, h->emit_tiles_max) == cudaSuccess &&
@@ -321,9 +346,11 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
                    const void *const *mom, const void *weights, double tol_x, double tol_p,
                    const pma_output *out, cudaStream_t st) {
   const int64_t C = h->cfg.n_cells;
+  uint32_t *cell_flags = out->cell_flags ? out->cell_flags : h->cell_flags;
   if (n == 0) {
     PMA_CUDA(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), st));
     if (out->count_dev) PMA_CUDA(h, cudaMemsetAsync(out->count_dev, 0, sizeof(int64_t), st));
+    if (out->cell_flags) PMA_CUDA(h, cudaMemsetAsync(out->cell_flags, 0, C * sizeof(uint32_t), st));
     return PMA_OK;
   }
   {
@@ -337,6 +364,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
     z.words[2] = kRadixMaxPasses * kRadixBins;
     z.p[3] = reinterpret_cast<uint32_t *>(h->bin_status);
     z.words[3] = (int64_t)h->bin_tiles * 2;
+    z.p[4] = cell_flags;
+    z.words[4] = C;
     const int64_t most = std::max<int64_t>(C, (int64_t)h->bin_tiles * 2);
     const int grid =
         (int)std::max<int64_t>(1, std::min<int64_t>((most + 255) / 256, (int64_t)h->sms * 4));
@@ -366,6 +395,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   b.block_list = h->block_list;
   b.block_count = &h->ctl->block_count;
   b.err = &h->ctl->err;
+  b.wait_ns = h->wait_ns ? h->wait_ns : kWaitNs;
+  b.withhold_tile = h->withhold_tile;
   b.scan_status = h->bin_status;
   b.scan_ticket = &h->ctl->bin_ticket;
   b.scan_tiles = h->bin_tiles;
@@ -422,6 +453,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.perm_final = h->perm_final;
   P.err = &h->ctl->err;
   P.stats = h->ctl->stats;
+  P.cell_flags = cell_flags;
   P.big_list = h->big_list;
   P.big_count = &h->ctl->big_count;
   P.big_next = &h->ctl->big_next;
@@ -552,6 +584,20 @@ int pma_get_timing(const pma_handle *h, float *ms, int n) {
   return PMA_OK;
 }
 
+int pma_set_wait_limit(pma_handle *h, int64_t wait_ns) {
+  if (!h || wait_ns < 0 || (wait_ns > 0 && wait_ns < 1000)) return PMA_ERR_INVALID_ARG;
+  h->wait_ns = (unsigned long long)wait_ns;
+  return PMA_OK;
+}
+
+int pma_test_status_of_bits(unsigned bits) { return status_of_bits(bits); }
+
+int pma_test_withhold_status(pma_handle *h, int tile) {
+  if (!h) return PMA_ERR_INVALID_ARG;
+  h->withhold_tile = tile < 0 ? -1 : tile;
+  return PMA_OK;
+}
+
 int pma_get_stats(const pma_handle *h, pma_stats *out) {
   if (!h || !out) return PMA_ERR_INVALID_ARG;
   *out = h->stats;
@@ -615,6 +661,9 @@ int pma_merge_host(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   if (out_host->index && n > 0)
     PMA_CUDA(h, cudaMemcpyAsync(out_host->index, S.out_index, n * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, st));
+  if (out_host->cell_flags)
+    PMA_CUDA(h, cudaMemcpyAsync(out_host->cell_flags, h->cell_flags,
+                                h->cfg.n_cells * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   PMA_CUDA(h, cudaStreamSynchronize(st));
   if (count_host) *count_host = M;
   return PMA_OK;

@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
   int total;
   int ex = block_exclusive_scan(sum, s_warp, &total);
   if (threadIdx.x < 32) {
-    const long long pre = warp_exclusive_prefix(a.scan_status, tile, total, a.err);
+    const long long pre = warp_exclusive_prefix(a.scan_status, tile, total, a.err, a.wait_ns,
+                                                tile != a.withhold_tile);
     if (threadIdx.x == 0) s_prefix = pre;
   }
   __syncthreads();
@@ -145,7 +146,7 @@ __device__ __forceinline__ unsigned radix_key(const BinArgs &a, int c) {
 
 // digit counts of every pass, and the first pass's look-back words cleared
 __global__ void __launch_bounds__(kRadixThreads) radix_prep_kernel(BinArgs a) {
-  if (*a.unsorted == 0) return;
+  if (*a.unsorted == 0 || timed_out(a.err)) return;
   __shared__ int s_count[kRadixMaxPasses][kRadixBins];
   for (int k = threadIdx.x; k < kRadixMaxPasses * kRadixBins; k += blockDim.x)
     (&s_count[0][0])[k] = 0;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_prep_kernel(BinArgs a) {
 // the digit, running per-warp counts), the CTA combines its warps, and each
 // digit's offset across tiles comes from a per-digit decoupled look-back.
 __global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, int p) {
-  if (*a.unsorted == 0) return;
+  if (*a.unsorted == 0 || timed_out(a.err)) return;
   __shared__ int s_tile;
   __shared__ int s_hist[kRadixWarps][kRadixBins];
   __shared__ int s_base[kRadixBins];
@@ -231,7 +232,8 @@ __global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, in
     s_hist[w][tid] = run;
     run += t;
   }
-  const long long before_tile = tile_exclusive_prefix(status + tid, tile, run, a.err, kRadixBins);
+  const long long before_tile =
+      tile_exclusive_prefix(status + tid, tile, run, a.err, kRadixBins, a.wait_ns);
   s_base[tid] = digit_base + (int)before_tile;
   __syncthreads();
 #pragma unroll

@@ -80,6 +80,7 @@ __device__ __forceinline__ int chunk_slots(unsigned hw, int upto) {
 template <bool EC>
 __global__ void __launch_bounds__(kEmitThreads) count_kernel(EmitArgs a) {
   __shared__ int s_warp[32];
+  if (timed_out(a.err)) return;
   const int64_t c0 = (int64_t)blockIdx.x * kEmitTile + (int64_t)threadIdx.x * kEmitChunk;
   int v = chunk_slots<EC>(load_heads(a.head, c0, a.n), kEmitChunk);
 #pragma unroll
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(kEmitThreads) count_kernel(EmitArgs a) {
 __global__ void __launch_bounds__(kScanCta) tiles_kernel(EmitArgs a) {
   __shared__ int s_warp[32];
   __shared__ long long s_carry;
+  if (timed_out(a.err)) return;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (int base = 0; base < a.tiles; base += kScanCta) {
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   __shared__ __align__(16) uint8_t s_head[kEmitTile];
   __shared__ int s_nmerged;
   __shared__ int2 s_merged[kEmitTile / 2 + 1];  // (offset in tile, output slot)
+  if (timed_out(a.err)) return;
   const int tid = threadIdx.x;
   const int D = a.dx + a.dp;
   const int64_t t0 = (int64_t)blockIdx.x * kEmitTile;

@@ -37,7 +37,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // can interleave their words).
 __device__ inline long long tile_exclusive_prefix(unsigned long long *status, int tile,
                                                   long long aggregate, unsigned *err,
-                                                  int stride = 1) {
+                                                  int stride = 1,
+                                                  unsigned long long wait_ns = kWaitNs) {
   if (tile == 0) {
     st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
     return 0;
@@ -53,7 +54,7 @@ __device__ inline long long tile_exclusive_prefix(unsigned long long *status, in
       unsigned long long now = global_ns();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > kWaitNs) {
+      } else if (now - t0 > wait_ns) {
         atomicOr(err, kErrTimeout);
         break;
       }
@@ -71,14 +72,19 @@ __device__ inline long long tile_exclusive_prefix(unsigned long long *status, in
 
 // Warp-wide version: called by all 32 lanes of one warp; examines 32
 // predecessors per step.  Returns the exclusive prefix of `tile` in every lane.
+// `publish` = false withholds this tile's status words (used only by the
+// failure-detection test: the tiles after it wait until wait_ns and report
+// kErrTimeout).
 __device__ inline long long warp_exclusive_prefix(unsigned long long *status, int tile,
-                                                  long long aggregate, unsigned *err) {
+                                                  long long aggregate, unsigned *err,
+                                                  unsigned long long wait_ns = kWaitNs,
+                                                  bool publish = true) {
   const int lane = threadIdx.x & 31;
   if (tile == 0) {
-    if (lane == 0) st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
+    if (lane == 0 && publish) st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
     return 0;
   }
-  if (lane == 0) st_release_u64(&status[tile], kFlagAgg | (unsigned long long)aggregate);
+  if (lane == 0 && publish) st_release_u64(&status[tile], kFlagAgg | (unsigned long long)aggregate);
   long long prefix = 0;
   int t = tile - 1;  // newest predecessor not yet summed
   unsigned long long t0 = 0;
@@ -94,7 +100,7 @@ __device__ inline long long warp_exclusive_prefix(unsigned long long *status, in
       unsigned long long now = global_ns();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > kWaitNs) {
+      } else if (now - t0 > wait_ns) {
         if (lane == 0) atomicOr(err, kErrTimeout);
         break;
       }
@@ -108,8 +114,16 @@ __device__ inline long long warp_exclusive_prefix(unsigned long long *status, in
     if (inc) break;
     t -= 32;
   }
-  if (lane == 0) st_release_u64(&status[tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+  if (lane == 0 && publish)
+    st_release_u64(&status[tile], kFlagInc | (unsigned long long)(prefix + aggregate));
   return prefix;
+}
+
+// true once a bounded wait of this call gave up: the kernels after it then
+// return at once (their inputs are incomplete), and the call reports
+// PMA_ERR_TIMEOUT
+__device__ __forceinline__ bool timed_out(const unsigned *err) {
+  return (*reinterpret_cast<const volatile unsigned *>(err) & kErrTimeout) != 0u;
 }
 
 // exclusive scan of one int per thread across the CTA (blockDim <= 1024);

@@ -36,6 +36,11 @@ enum Stat {
   kStDegenerate,
   kStBig,
   kStSorted,
+  kStNearStop,     // decisions flagged near a tie, by kind
+  kStNearArgmax,
+  kStNearCut,
+  kStRecheck,      // FP32 decisions taken again in FP64
+  kStCellsFlagged, // cells with at least one near-tie flag
   kStCount
 };
 
@@ -76,11 +81,12 @@ struct Problem {
                           // or all null (then the emit step gathers)
   unsigned *err;          // device status word
   unsigned long long *stats;
+  uint32_t *cell_flags;   // [n_cells] near-tie bits of each cell (zeroed per call)
   // big cells: cells above `cap` are cut in global memory first
   int32_t *big_list;
   int32_t *big_count;
   int32_t *big_next;
-  int4 *pieces;           // {begin, end, depth, 0}
+  int4 *pieces;           // {begin, end, depth, cell}
   int32_t *piece_count;
   int32_t *perm_tmp;
   int32_t max_pieces;
@@ -146,6 +152,7 @@ struct Acc<float> {
   }
   __device__ __forceinline__ float hi() const { return s; }
   __device__ __forceinline__ float lo() const { return -c; }
+  __device__ __forceinline__ float val() const { return __fsub_rn(s, c); }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
@@ -206,24 +213,54 @@ struct Moments {
 
 // ------------------------------------------------------------- decisions
 
+// Near-tie bits, recorded per cell: a decision taken within rounding of the
+// opposite outcome (Step 3 stop test, Step 4 runner-up axis, Step 5 particle
+// at the cut value), and kRechecked when an FP32 decision was too close to
+// call and was taken again in FP64 from the particles.
+constexpr unsigned kNearStop = 1u;
+constexpr unsigned kNearArgmax = 2u;
+constexpr unsigned kNearCut = 4u;
+constexpr unsigned kRechecked = 8u;
+// FP64 near-tie threshold on squared CVs (|Delta^2 - T^2| <= 4e-9 T^2 covers
+// |Delta - T| <= 1e-9 T with room for the rounding of either side)
+constexpr double kNearRel2 = 4e-9;
+
 struct Cut {
-  int leaf;   // Step 3 stop test passed
-  int k;      // Step 4 axis
-  double Q;   // Step 5 centroid coordinate on axis k (FP64)
-  float Qt;   // largest float <= Q (FP32 storage: q <= Q  <=>  q <= Qt)
+  int leaf;        // Step 3 stop test passed
+  int k;           // Step 4 axis
+  int unsure;      // FP32 decision closer than its error bound: retake in FP64
+  unsigned near;   // kNearStop | kNearArgmax (FP64 decisions)
+  double Q;        // Step 5 centroid coordinate on axis k (FP64 decisions)
+  double Qlo, Qhi; // FP64 decisions: particles in [Qlo, Qhi] are cut near-ties
+  float Qt;        // largest float <= Q (FP32 storage: q <= Q  <=>  q <= Qt)
+  float Qlo_f, Qhi_f;  // FP32 storage: particles in [Qlo_f, Qhi_f] make the cut
+                       // uncertain (FP32 decisions) or are near-ties (FP64 ones)
 };
 
-// Steps 3-5 in FP64 from moment values (W, m1, m2 about the shift s).
-// VAR = false: the paper's rule only; true: the variants in P.variant.
-template <int D, bool VAR = true>
-__device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const double *m1,
-                                           const double *m2, const double *s) {
+__device__ __forceinline__ Cut cut_none() {
   Cut c;
   c.leaf = 1;
   c.k = 0;
+  c.unsure = 0;
+  c.near = 0u;
+  c.Q = c.Qlo = c.Qhi = 0.0;
+  c.Qt = c.Qlo_f = c.Qhi_f = 0.f;
+  return c;
+}
+
+// Steps 3-5 in FP64 from moment values (W, m1, m2 about the shift s) of a
+// subset of m particles.  VAR = false: the paper's rule only; true: the
+// variants in P.variant.  Near-tie bits: some |Delta_l^2 - T_l^2| within
+// kNearRel2 T_l^2 (stop), the runner-up axis within kNearRel2 of the chosen
+// one (argmax).  The cut band is 64 m eps (|s_k| + sqrt(m2_k / W)), which is
+// at least 64 m eps (sum w |q_k|) / W by Cauchy-Schwarz.
+template <int D, bool VAR = true, class PP = Problem>
+__device__ __forceinline__ Cut decide_fp64(const PP &P, double W, const double *m1,
+                                           const double *m2, const double *s, int m) {
+  Cut c = cut_none();
   const bool normd = VAR && (P.variant & kVarNormalized) != 0;
   const bool pnorm = VAR && (P.variant & kVarPNorm) != 0;
-  double bestV = -1.0, bestDen = 1.0;
+  double bestV = -1.0, bestDen = 1.0, secV = -1.0, secDen = 1.0;
   double W2 = W * W;
   double denN = 0.0;  // (W |P|)^2 for the momentum-norm variant
   if (pnorm) {
@@ -247,40 +284,69 @@ __device__ __forceinline__ Cut decide_fp64(const Problem &P, double W, const dou
       tol2 = P.tol2_p;
     }
     // Delta_l <= T  <=>  V <= T^2 den  (den = 0: only V = 0 passes)
-    if (!(V <= tol2 * den)) c.leaf = 0;
+    const double t = tol2 * den;
+    if (!(V <= t)) c.leaf = 0;
+    if (t > 0.0 && fabs(V - t) <= kNearRel2 * t) c.near |= kNearStop;
     // first maximum of V / kden = Delta_l^2, or (Delta_l / T_l)^2 for the
     // normalised variant; kden = 0 is +infinity, and V = 0 counts as 0
-    double kden = normd ? den * tol2 : den;
+    double kden = normd ? t : den;
     if (V == 0.0) kden = 1.0;
     if (bestV < 0.0 || V * bestDen > bestV * kden) {
+      secV = bestV;
+      secDen = bestDen;
       bestV = V;
       bestDen = kden;
       c.k = l;
+    } else if (secV < 0.0 || V * secDen > secV * kden) {
+      secV = V;
+      secDen = kden;
     }
   }
-  double Q = s[0];
+  if (c.leaf) {
+    c.near &= kNearStop;
+    return c;
+  }
+  // the runner-up within kNearRel2 of the chosen axis (two infinite scores tie)
+  if (secV >= 0.0 && secV * bestDen >= bestV * secDen * (1.0 - kNearRel2)) c.near |= kNearArgmax;
+  double Q = s[0], sk = s[0], m2k = m2[0];
 #pragma unroll
   for (int l = 0; l < D; ++l)
-    if (l == c.k) Q = s[l] + m1[l] / W;
+    if (l == c.k) {
+      Q = s[l] + m1[l] / W;
+      sk = s[l];
+      m2k = m2[l];
+    }
+  const float tau = 64.0f * (float)m * 2.220446049250313e-16f *
+                    (fabsf((float)sk) + sqrtf(fmaxf((float)m2k, 0.f) / (float)W)) * 1.0625f;
   c.Q = Q;
+  c.Qlo = Q - (double)tau;
+  c.Qhi = Q + (double)tau;
   c.Qt = __double2float_rd(Q);
+  c.Qlo_f = __double2float_rd(c.Qlo);
+  c.Qhi_f = __double2float_ru(c.Qhi);
   return c;
 }
 
-// Step 3-5 for compensated FP32 moments.  The stop test and the axis choice
-// are evaluated in FP32 with an error bound; when a comparison is closer
-// than the bound the FP64 evaluation of the same sums decides.  The cut value
-// is computed as a double-float (hi + lo) and rounded down to float.
+// Steps 3-5 for compensated FP32 moments of a subset of m particles, with a
+// certificate.  Every comparison is made in FP32 together with a bound on its
+// error: the sums W, m1_l, m2_l are off by at most kk times W, sqrt(W m2_l)
+// (which bounds sum w |q - s| by Cauchy-Schwarz) and m2_l, where kk follows
+// from the run length `run`, the most terms one lane added in plain FP32
+// (the runs are combined exactly).  When a comparison lies within its bound
+// the result has unsure = 1, and the caller takes the decision again in FP64
+// from the particles themselves; otherwise it is the exact-arithmetic
+// decision on the stored values.  The cut value Q = s_k + m1_k / W is formed
+// as a double-float and rounded down to float; [Qlo_f, Qhi_f] contains the
+// exact Q, so only a particle inside that band can fall on the wrong side.
 template <int D, bool VAR = true>
 __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<float, D> &M,
-                                            const float *s) {
-  const float g = 1.0f / (1 << 17);  // error budget relative to the terms
-  float W = M.W.hi();
-  float W2 = W * W;
-  Cut c;
-  c.leaf = 1;
-  c.k = 0;
-  bool sure = true;
+                                            const float *s, int run) {
+  constexpr float u = 1.0f / (1 << 24);
+  const float kk = (float)(run + 8) * (2.0f * u);
+  const float inf = __int_as_float(0x7f800000);
+  const float W = M.W.val();
+  const float eW = kk * W;
+  Cut c = cut_none();
   const bool normd = VAR && (P.variant & kVarNormalized) != 0;
   const bool pnorm = VAR && (P.variant & kVarPNorm) != 0;
   // momentum-norm variant: (W |P|)^2 and its error bound
@@ -289,84 +355,82 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
 #pragma unroll
     for (int l = 0; l < D; ++l)
       if (l >= P.dx) {
-        const float m1 = M.m1[l].hi();
+        const float m1 = M.m1[l].val(), m2 = fmaxf(M.m2[l].val(), 0.f);
+        const float em1 = kk * sqrtf(W * m2) + u * fabsf(m1);
         const float Pw = fmaf(s[l], W, m1);
-        const float eP = g * (fabsf(s[l] * W) + fabsf(m1));
+        const float eP = fabsf(s[l]) * eW + em1 + 2.f * u * (fabsf(s[l] * W) + fabsf(m1));
         denN = fmaf(Pw, Pw, denN);
         eDN += 2.f * fabsf(Pw) * eP + eP * eP;
       }
-    eDN += g * denN;
+    eDN = (eDN + 8.f * u * denN) * 1.0625f;
   }
-  // first and second largest V / kden: Delta^2 (position: V / (L W)^2,
-  // momentum: V / (W P)^2), or (Delta / T)^2 for the normalised variant;
-  // kden = 0 is +infinity unless V = 0
-  float r1 = -1.f, r2 = -1.f;
+  bool sure = true;
+  // the axis of the largest score (point estimate), a lower bound of its
+  // score and an upper bound of every other axis' score
+  float best = -1.f, bestLo = 0.f, bestHi = 0.f, otherHi = 0.f;
 #pragma unroll
   for (int l = 0; l < D; ++l) {
-    float m1 = M.m1[l].hi(), m2 = M.m2[l].hi();
-    float a = m2 * W, b = m1 * m1;
-    float V = fmaxf(a - b, 0.f);
-    float eV = g * (fabsf(a) + b);
+    const float m1 = M.m1[l].val(), m2 = fmaxf(M.m2[l].val(), 0.f);
+    const float a = m2 * W, b = m1 * m1;
+    const float V = fmaxf(a - b, 0.f);
+    const float em1 = kk * sqrtf(a) + u * fabsf(m1);
+    const float eV =
+        (2.f * kk * a + 2.f * fabsf(m1) * em1 + em1 * em1 + 4.f * u * (a + b)) * 1.0625f;
     float den, eD, tol2;
     if (l < P.dx) {
-      den = P.L2f[l] * W2;
-      eD = g * den;
+      den = P.L2f[l] * (W * W);
+      eD = (2.f * kk + 4.f * u) * den * 1.0625f;
       tol2 = P.tol2_xf;
     } else if (pnorm) {
       den = denN;
       eD = eDN;
       tol2 = P.tol2_pf;
     } else {
-      float Pw = fmaf(s[l], W, m1);
-      float eP = g * (fabsf(s[l] * W) + fabsf(m1));
+      const float Pw = fmaf(s[l], W, m1);
+      const float eP = fabsf(s[l]) * eW + em1 + 2.f * u * (fabsf(s[l] * W) + fabsf(m1));
       den = Pw * Pw;
-      eD = 2.f * fabsf(Pw) * eP + eP * eP + g * den;
+      eD = (2.f * fabsf(Pw) * eP + eP * eP + 2.f * u * den) * 1.0625f;
       tol2 = P.tol2_pf;
     }
-    float f = V - tol2 * den;
-    if (fabsf(f) <= eV + tol2 * eD) sure = false;
+    // Step 3: Delta_l <= T  <=>  V <= T^2 den
+    const float t = tol2 * den;
+    const float f = V - t;
     if (f > 0.f) c.leaf = 0;
-    const float kden = normd ? den * tol2 : den, eK = normd ? eD * tol2 : eD;
-    float r;
-    if (V == 0.f)
-      r = 0.f;
-    else if (kden <= eK)
-      r = __int_as_float(0x7f800000);
-    else
-      r = __fdividef(V, kden);
-    if (V != 0.f && (V <= eV || kden <= eK)) sure = false;
-    if (r > r1) {
-      r2 = r1;
-      r1 = r;
+    if (!(fabsf(f) > eV + tol2 * eD + 2.f * u * (V + t))) sure = false;
+    // Step 4: score V / kden (Delta^2, or (Delta / T)^2 normalised)
+    const float kden = normd ? t : den, eK = normd ? tol2 * eD : eD;
+    const float r = V == 0.f ? 0.f : (kden > 0.f ? __fdividef(V, kden) : inf);
+    const float lo =
+        V > eV ? (kden + eK > 0.f ? __fdividef(V - eV, kden + eK) * (1.f - 8.f * u) : inf) : 0.f;
+    const float hi = (V + eV == 0.f)
+                         ? 0.f
+                         : (kden > eK ? __fdividef(V + eV, kden - eK) * (1.f + 8.f * u) : inf);
+    if (r > best) {
+      otherHi = fmaxf(otherHi, bestHi);
+      best = r;
+      bestLo = lo;
+      bestHi = hi;
       c.k = l;
-    } else if (r > r2) {
-      r2 = r;
+    } else {
+      otherHi = fmaxf(otherHi, hi);
     }
   }
-  // the runner-up axis within the error budget: FP64 decides
-  if (!c.leaf && r2 >= r1 * (1.f - 16.f * g)) sure = false;
+  if (!c.leaf && !(bestLo > otherHi)) sure = false;
   if (!sure) {
-    double W64 = M.W.value(), m1d[D], m2d[D], sd[D];
-#pragma unroll
-    for (int l = 0; l < D; ++l) {
-      m1d[l] = M.m1[l].value();
-      m2d[l] = M.m2[l].value();
-      sd[l] = (double)s[l];
-    }
-    Cut d = decide_fp64<D, VAR>(P, W64, m1d, m2d, sd);
-    d.Q = 0.0;
-    c.leaf = d.leaf;
-    c.k = d.k;
+    c.unsure = 1;
+    c.leaf = 0;
+    return c;
   }
   if (c.leaf) return c;
   // cut value Q = s_k + m1_k / W as a double-float, then rounded down
-  float sk = s[0], m1h = M.m1[0].hi(), m1l = M.m1[0].lo();
+  float sk = s[0], m1h = M.m1[0].hi(), m1l = M.m1[0].lo(), m2k = M.m2[0].val();
 #pragma unroll
   for (int l = 0; l < D; ++l)
     if (l == c.k) {
       sk = s[l];
       m1h = M.m1[l].hi();
       m1l = M.m1[l].lo();
+      m2k = M.m2[l].val();
     }
   float Wh = M.W.hi(), Wl = M.W.lo();
   float q0 = __fdiv_rn(m1h, Wh);
@@ -384,7 +448,12 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   c.Qt = (Ql < 0.f) ? __int_as_float(__float_as_int(Qh) - (Qh > 0.f ? 1 : (Qh < 0.f ? -1 : 0)))
                     : Qh;
   if (Qh == 0.f && Ql < 0.f) c.Qt = -__int_as_float(1);  // largest float below zero
-  c.Q = 0.0;  // the float path compares against Qt only
+  // |Q - Q_exact| <= (e_m1 + |m1 / W| e_W) / W, plus the double-float's own
+  // rounding and the rounding of this bound
+  const float em1k = kk * sqrtf(fmaxf(m2k, 0.f) * W) + u * fabsf(m1h);
+  const float eQ = (em1k + fabsf(q0) * eW) / W * 1.0625f + 4.f * u * fabsf(Qh) + 1e-37f;
+  c.Qlo_f = __fsub_rd(Qh, eQ);
+  c.Qhi_f = __fadd_ru(Qh, eQ);
   return c;
 }
 

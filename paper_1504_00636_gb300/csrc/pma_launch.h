@@ -39,6 +39,9 @@ struct BinArgs {
   int32_t *block_list;
   int32_t *block_count;
   unsigned *err;
+  unsigned long long wait_ns;       // limit of every bounded wait
+  int32_t withhold_tile;            // failure-detection test: this scan tile never
+                                    // publishes its status (-1: none)
   unsigned long long *scan_status;  // [scan tiles]
   int32_t *scan_ticket;
   int32_t scan_tiles;

@@ -104,7 +104,54 @@ __device__ void warp_split(const Problem &P, const Tile<T, D> &S, const int32_t 
     M.add(S.col(par, D)[i], q, s);
   }
   M.warp_allreduce();
-  Cut c = Decider<T, D>::run(P, M, s);
+  Cut c = Decider<T, D>::run(P, M, s, e - b, (e - b + 31) / 32);
+  // FP32 storage: a decision or a cut too close to call is taken again with
+  // FP64 sums of the set (warp-uniform: every lane holds the same sums)
+  bool exact = sizeof(T) == 8;
+  const int np = par ^ 1;
+  int cntL = 0, cntR = 0;
+  for (;;) {
+    if (c.unsure) {
+      Moments<double, D> X;
+      X.zero();
+      for (int i = b + lane; i < e; i += 32) {
+        T q[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) q[l] = S.col(par, l)[i];
+        add_exact<T, D>(X, S.col(par, D)[i], q, s);
+      }
+      X.warp_allreduce();
+      c = decide_exact<T, D, true>(P, X, s, e - b);
+      exact = true;
+    }
+    if (c.leaf) break;
+    const T *qk = S.col(par, c.k);
+    cntL = cntR = 0;
+    bool nr = false;
+    const unsigned lt = lanemask_lt();
+    for (int base = b; base < e; base += 32) {
+      int i = base + lane;
+      bool valid = i < e;
+      const T q = qk[valid ? i : b];
+      bool lft = valid && Decider<T, D>::left(q, c);
+      nr |= valid && Decider<T, D>::near(q, c);
+      unsigned bl = __ballot_sync(0xffffffffu, lft);
+      unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+      if (valid) {
+        int dst = lft ? (b + cntL + __popc(bl & lt)) : (e - 1 - cntR - __popc(br & lt));
+#pragma unroll
+        for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
+        S.id[np][dst] = S.id[par][i];
+      }
+      cntL += __popc(bl);
+      cntR += __popc(br);
+    }
+    if (__any_sync(0xffffffffu, nr) && !exact) {
+      c.unsure = 1;
+      continue;
+    }
+    break;
+  }
   if (c.leaf) {
     emit_leaf_warp<T, D>(P, S, perm, gb, b, e, par, M, s, lane);
     if (lane == 0) {
@@ -112,25 +159,6 @@ __device__ void warp_split(const Problem &P, const Tile<T, D> &S, const int32_t 
       atomicAdd(&st[kStDepth], (unsigned long long)it.depth * (e - b));
     }
     return;
-  }
-  const int np = par ^ 1;
-  const T *qk = S.col(par, c.k);
-  int cntL = 0, cntR = 0;
-  const unsigned lt = lanemask_lt();
-  for (int base = b; base < e; base += 32) {
-    int i = base + lane;
-    bool valid = i < e;
-    bool lft = valid && Decider<T, D>::left(qk[valid ? i : b], c);
-    unsigned bl = __ballot_sync(0xffffffffu, lft);
-    unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
-    if (valid) {
-      int dst = lft ? (b + cntL + __popc(bl & lt)) : (e - 1 - cntR - __popc(br & lt));
-#pragma unroll
-      for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
-      S.id[np][dst] = S.id[par][i];
-    }
-    cntL += __popc(bl);
-    cntR += __popc(br);
   }
   __syncwarp();
   if (cntL == 0 || cntR == 0) {
@@ -199,22 +227,49 @@ __device__ void thread_finish(const Problem &P, const Tile<T, D> &S, const int32
       for (int l = 0; l < D; ++l) q[l] = S.col(par, l)[i];
       M.add(S.col(par, D)[i], q, s);
     }
-    Cut c = Decider<T, D>::run(P, M, s);
+    Cut c = Decider<T, D>::run(P, M, s, e - b, e - b);
+    // FP32 storage: a decision or a cut too close to call is taken again
+    // with FP64 sums of the set
+    bool exact = sizeof(T) == 8;
+    const int np = par ^ 1;
+    int cntL = 0, cntR = 0;
+    for (;;) {
+      if (c.unsure) {
+        Moments<double, D> X;
+        X.zero();
+        for (int i = b; i < e; ++i) {
+          T q[D];
+#pragma unroll
+          for (int l = 0; l < D; ++l) q[l] = S.col(par, l)[i];
+          add_exact<T, D>(X, S.col(par, D)[i], q, s);
+        }
+        c = decide_exact<T, D, true>(P, X, s, e - b);
+        exact = true;
+      }
+      if (c.leaf) break;
+      const T *qk = S.col(par, c.k);
+      cntL = cntR = 0;
+      bool nr = false;
+      for (int i = b; i < e; ++i) {
+        const T q = qk[i];
+        bool lft = Decider<T, D>::left(q, c);
+        nr |= Decider<T, D>::near(q, c);
+        int dst = lft ? (b + cntL++) : (e - 1 - cntR++);
+#pragma unroll
+        for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
+        S.id[np][dst] = S.id[par][i];
+      }
+      if (nr && !exact) {
+        c.unsure = 1;
+        continue;
+      }
+      break;
+    }
     if (c.leaf) {
       emit_leaf_thread<T, D>(P, S, perm, gb, b, e, par, M, s);
       cnt[0] += 1;
       cnt[1] += (unsigned long long)it.depth * (e - b);
       continue;
-    }
-    const int np = par ^ 1;
-    const T *qk = S.col(par, c.k);
-    int cntL = 0, cntR = 0;
-    for (int i = b; i < e; ++i) {
-      bool lft = Decider<T, D>::left(qk[i], c);
-      int dst = lft ? (b + cntL++) : (e - 1 - cntR++);
-#pragma unroll
-      for (int l = 0; l <= D; ++l) S.col(np, l)[dst] = S.col(par, l)[i];
-      S.id[np][dst] = S.id[par][i];
     }
     if (cntL == 0 || cntR == 0) {
       emit_leaf_thread<T, D>(P, S, perm, gb, b, e, np, M, s);
@@ -240,31 +295,36 @@ struct BlockMoments {
   Moments<T, D> part[32];
 };
 
-// block-wide moments of perm[b, e) about s; result valid in all threads
-template <typename T, int D>
-__device__ Moments<T, D> block_moments(const Problem &P, const int32_t *perm, int64_t b,
-                                       int64_t e, const T *s, BlockMoments<T, D> &sh,
+// block-wide moments of perm[b, e) about s, accumulated in A (T, or double
+// for the FP64 recheck of an FP32 decision); result valid in all threads
+template <typename A, typename T, int D>
+__device__ Moments<A, D> block_moments(const Problem &P, const int32_t *perm, int64_t b,
+                                       int64_t e, const T *s, BlockMoments<A, D> &sh,
                                        bool &bad) {
-  Moments<T, D> M;
+  Moments<A, D> M;
   M.zero();
+  A sa[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) sa[l] = (A)s[l];
   for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
     int src = perm[i];
-    T q[D];
+    A q[D];
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-      q[l] = StoreOf<T>::load(P.q[l], src);
-      bad |= !finite_val(q[l]);
+      const T x = StoreOf<T>::load(P.q[l], src);
+      bad |= !finite_val(x);
+      q[l] = (A)x;
     }
     T w = StoreOf<T>::load(P.w, src);
     bad |= !(w > T(0)) || !finite_val(w);
-    M.add(w, q, s);
+    M.add((A)w, q, sa);
   }
   M.warp_allreduce();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   if (lane == 0) sh.part[warp] = M;
   __syncthreads();
-  Moments<T, D> R = sh.part[0];
+  Moments<A, D> R = sh.part[0];
   for (int k = 1; k < nw; ++k) R.merge(sh.part[k]);
   return R;
 }
@@ -274,10 +334,11 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
   constexpr int kStack = 1024;
   __shared__ int4 stk[kStack];
   __shared__ int s_sp, s_ticket;
-  __shared__ BlockMoments<T, D> sh;
+  __shared__ __align__(16) BlockMoments<T, D> sh;
   __shared__ int s_wcnt[2][16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
+  if (timed_out(P.err)) return;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_ticket = atomicAdd(P.big_next, 1);
@@ -289,7 +350,7 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
     if (*P.unsorted == 0)
       for (int64_t i = gb + tid; i < ge; i += blockDim.x) P.perm[i] = (int32_t)i;
     if (tid == 0) {
-      stk[0] = make_int4((int)gb, (int)ge, 0, 0);
+      stk[0] = make_int4((int)gb, (int)ge, 0, c);
       s_sp = 1;
       atomicAdd(&P.stats[kStBig], 1ull);
       atomicAdd(&P.stats[kStCellsMerged], 1ull);
@@ -305,52 +366,89 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
       const int first = P.perm[b];
 #pragma unroll
       for (int l = 0; l < D; ++l) s[l] = StoreOf<T>::load(P.q[l], first);
-      bool bad = false;
-      Moments<T, D> M = block_moments<T, D>(P, P.perm, b, e, s, sh, bad);
-      if (bad) set_error(P.err, kErrInput);
-      Cut cut = Decider<T, D>::run(P, M, s);
+      // Steps 2-6 on perm[b, e).  FP32 storage: a decision or a cut too close
+      // to call in FP32 is taken again with FP64 sums (exact = true); the
+      // control flow is the same in every thread (identical block sums).
+      const int mset = (int)(e - b);
+      bool exact = sizeof(T) == 8;
+      Cut cut;
       int64_t nL = 0;
-      if (!cut.leaf) {
-        // stable-left / reversed-right partition of perm[b, e) into perm_tmp
-        int64_t cntL = 0, cntR = 0;
-        for (int64_t base = b; base < e; base += blockDim.x) {
-          int64_t i = base + tid;
-          bool valid = i < e;
-          int src = valid ? P.perm[i] : 0;
-          bool lft = valid && Decider<T, D>::left(StoreOf<T>::load(P.q[cut.k], src), cut);
-          unsigned bl = __ballot_sync(0xffffffffu, lft);
-          unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
-          __syncthreads();
-          if (lane == 0) {
-            s_wcnt[0][warp] = __popc(bl);
-            s_wcnt[1][warp] = __popc(br);
-          }
-          __syncthreads();
-          int offL = 0, offR = 0, totL = 0, totR = 0;
-          for (int k = 0; k < nw; ++k) {
-            if (k < warp) {
-              offL += s_wcnt[0][k];
-              offR += s_wcnt[1][k];
+      for (;;) {
+        bool bad = false;
+        if (sizeof(T) == 4 && exact) {
+          Moments<double, D> M = block_moments<double, T, D>(
+              P, P.perm, b, e, s, reinterpret_cast<BlockMoments<double, D> &>(sh), bad);
+          cut = decide_exact<T, D, true>(P, M, s, mset);
+        } else {
+          Moments<T, D> M = block_moments<T, T, D>(P, P.perm, b, e, s, sh, bad);
+          cut = Decider<T, D>::run(P, M, s, mset, (int)((e - b + blockDim.x - 1) / blockDim.x));
+        }
+        if (bad) set_error(P.err, kErrInput);
+        if (cut.unsure) {
+          exact = true;
+          if (tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
+          continue;
+        }
+        unsigned ev = cut.near;
+        nL = 0;
+        bool nr = false;
+        if (!cut.leaf) {
+          // stable-left / reversed-right partition of perm[b, e) into perm_tmp
+          int64_t cntL = 0, cntR = 0;
+          for (int64_t base = b; base < e; base += blockDim.x) {
+            int64_t i = base + tid;
+            bool valid = i < e;
+            int src = valid ? P.perm[i] : 0;
+            const T q = StoreOf<T>::load(P.q[cut.k], src);
+            bool lft = valid && Decider<T, D>::left(q, cut);
+            nr |= valid && Decider<T, D>::near(q, cut);
+            unsigned bl = __ballot_sync(0xffffffffu, lft);
+            unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+            __syncthreads();
+            if (lane == 0) {
+              s_wcnt[0][warp] = __popc(bl);
+              s_wcnt[1][warp] = __popc(br);
             }
-            totL += s_wcnt[0][k];
-            totR += s_wcnt[1][k];
+            __syncthreads();
+            int offL = 0, offR = 0, totL = 0, totR = 0;
+            for (int k = 0; k < nw; ++k) {
+              if (k < warp) {
+                offL += s_wcnt[0][k];
+                offR += s_wcnt[1][k];
+              }
+              totL += s_wcnt[0][k];
+              totR += s_wcnt[1][k];
+            }
+            if (valid) {
+              int64_t dst = lft ? (b + cntL + offL + __popc(bl & lt))
+                                : (e - 1 - cntR - offR - __popc(br & lt));
+              P.perm_tmp[dst] = src;
+            }
+            cntL += totL;
+            cntR += totR;
           }
-          if (valid) {
-            int64_t dst = lft ? (b + cntL + offL + __popc(bl & lt))
-                              : (e - 1 - cntR - offR - __popc(br & lt));
-            P.perm_tmp[dst] = src;
+          nr = __syncthreads_or(nr) != 0;
+          if (nr && !exact) {
+            exact = true;  // perm[b, e) is untouched until the copy below
+            if (tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
+            continue;
           }
-          cntL += totL;
-          cntR += totR;
+          if (nr) ev |= kNearCut;
+          for (int64_t i = b + tid; i < e; i += blockDim.x) P.perm[i] = P.perm_tmp[i];
+          nL = cntL;
+          if (cntL == 0 || cntR == 0) {
+            cut.leaf = 1;
+            if (tid == 0) atomicAdd(&P.stats[kStDegenerate], 1ull);
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        for (int64_t i = b + tid; i < e; i += blockDim.x) P.perm[i] = P.perm_tmp[i];
-        nL = cntL;
-        if (cntL == 0 || cntR == 0) {
-          cut.leaf = 1;
-          if (tid == 0) atomicAdd(&P.stats[kStDegenerate], 1ull);
+        if (ev && tid == 0) {
+          if (ev & kNearStop) atomicAdd(&P.stats[kStNearStop], 1ull);
+          if (ev & kNearArgmax) atomicAdd(&P.stats[kStNearArgmax], 1ull);
+          if (ev & kNearCut) atomicAdd(&P.stats[kStNearCut], 1ull);
+          if (atomicOr(&P.cell_flags[c], ev) == 0u) atomicAdd(&P.stats[kStCellsFlagged], 1ull);
         }
-        __syncthreads();
+        break;
       }
       if (cut.leaf) {
         for (int64_t i = b + tid; i < e; i += blockDim.x) {
@@ -367,8 +465,8 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
       }
       if (tid == 0) {
         atomicAdd(&P.stats[kStSplits], 1ull);
-        int4 ch[2] = {make_int4((int)b, (int)(b + nL), it.z + 1, 0),
-                      make_int4((int)(b + nL), (int)e, it.z + 1, 0)};
+        int4 ch[2] = {make_int4((int)b, (int)(b + nL), it.z + 1, c),
+                      make_int4((int)(b + nL), (int)e, it.z + 1, c)};
         for (int h = 1; h >= 0; --h) {
           int n = ch[h].y - ch[h].x;
           if (n > P.cap) {
@@ -450,17 +548,18 @@ cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st) {
 namespace pma {
 
 struct NoAllocScratch {
-  // must be zero when a call starts
-  unsigned long long status[PMA_NOALLOC_MAX_CELLS];
+  // must be zero when a call starts: the header, and the look-back words of
+  // the call's n_cells cells
   int32_t ticket;
   unsigned err;
   int64_t count;
   unsigned long long stats[kStCount];
+  unsigned long long status[PMA_NOALLOC_MAX_CELLS];
   // written before being read within a call
   int32_t perm_final[PMA_NOALLOC_MAX_N];
   uint8_t head[PMA_NOALLOC_MAX_N];
 };
-constexpr size_t kNoAllocZeroBytes = offsetof(NoAllocScratch, perm_final);
+constexpr size_t kNoAllocHeaderBytes = offsetof(NoAllocScratch, status);
 constexpr unsigned kErrCellTooBig = 8u;
 
 // Every device that loads the library holds this array until the process exits.
@@ -622,14 +721,21 @@ __global__ void __launch_bounds__(256) noalloc_kernel(Problem P, NoAllocScratch 
       if (!h) continue;
       o.cell[slot] = c;
       if (h == kHeadSingle) {
-        for (int l = 0; l < P.dx; ++l)
-          static_cast<T *>(o.pos[l])[slot] = StoreOf<T>::load(P.q[l], orig);
+        // a particle copied as it is (a one-particle set or a cell passed
+        // through): every loaded value is checked, as in pma_merge
+        bool bad = false;
+        for (int l = 0; l < P.dx; ++l) {
+          const T x = StoreOf<T>::load(P.q[l], orig);
+          bad |= !finite_val(x);
+          static_cast<T *>(o.pos[l])[slot] = x;
+        }
         for (int l = 0; l < P.D - P.dx; ++l) {
           T x = StoreOf<T>::load(P.q[P.dx + l], orig);
+          bad |= !finite_val(x);
           o.mom[l][slot] = sizeof(T) == 4 ? f2d_exact((float)x) : (double)x;
         }
         T w = StoreOf<T>::load(P.w, orig);
-        if (!(w > T(0)) || !finite_val(w)) atomicOr(&Sc->err, kErrInput);
+        if (bad || !(w > T(0)) || !finite_val(w)) atomicOr(&Sc->err, kErrInput);
         o.w[slot] = sizeof(T) == 4 ? f2d_exact((float)w) : (double)w;
       } else {
         // merged set: FP64 sums over its members (positions up to the next
@@ -689,6 +795,9 @@ extern "C" int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t
                                  const pma_output *out, int64_t *count_host, void *stream) {
   using namespace pma;
   if (!cfg || !out) return PMA_ERR_INVALID_ARG;
+  // only the paper's rule and plain Step 7: a variant or energy flag would be
+  // silently ignored here, so it is refused (PMA_FLAG_NO_INDEX is accepted)
+  if (cfg->flags & ~PMA_FLAG_NO_INDEX) return PMA_ERR_INVALID_ARG;
   if (cfg->dx < 1 || cfg->dx > 3 || cfg->dp < 1 || cfg->dp > 3 || cfg->n_min < 0 ||
       cfg->n_cells < 1 || (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED))
     return PMA_ERR_INVALID_ARG;
@@ -731,7 +840,9 @@ extern "C" int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t
     addr = g_noalloc_addr[dev];
   }
   NoAllocScratch *Sc = static_cast<NoAllocScratch *>(addr);
-  if (cudaMemsetAsync(Sc, 0, kNoAllocZeroBytes, st) != cudaSuccess) return PMA_ERR_CUDA;
+  if (cudaMemsetAsync(Sc, 0, kNoAllocHeaderBytes + (size_t)cfg->n_cells * sizeof(unsigned long long),
+                      st) != cudaSuccess)
+    return PMA_ERR_CUDA;
   if (n == 0) {
     if (out->count_dev && cudaMemsetAsync(out->count_dev, 0, sizeof(int64_t), st) != cudaSuccess)
       return PMA_ERR_CUDA;
@@ -774,7 +885,7 @@ extern "C" int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t
     o.mom[a] = out->mom[a];
   }
   o.w = out->w;
-  o.index = out->index;
+  o.index = (cfg->flags & PMA_FLAG_NO_INDEX) ? nullptr : out->index;
   o.count_dev = out->count_dev;
   const int grid = (int)std::min<int64_t>(cfg->n_cells, g_noalloc_sms[dev]);
   cudaError_t e;

@@ -24,6 +24,7 @@
 // translation units (warp.cu, warp_var.cu).
 #pragma once
 
+#include "lookback.cuh"
 #include "pma_device.cuh"
 #include "pma_launch.h"
 #include "split_common.cuh"
@@ -82,6 +83,8 @@ struct WarpTile {
   int *top;        // [kClasses] stack heights
   uint16_t *soff;  // [kClasses] first entry of each stack (class 1: the end
                    // of the region shared with class 0), [kClasses] capacities
+  int *ev;         // [kEvWords]: near-tie bits of the current unit, then the
+                   // CTA's counts of near-ties by kind and of FP64 rechecks
   void *wide;      // wide rounds: [kMaxTeam] partial moments, [kMaxTeam] counts
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
@@ -93,19 +96,27 @@ struct WarpTile {
   __device__ __forceinline__ int stk_cap(int c) const { return soff[kClasses + c]; }
 };
 
+// control words after the class stack heights: the unit ticket, then kEvWords
+// event words (unit near-tie bits; near-stop, near-argmax, near-cut and
+// recheck counts)
+constexpr int kEvWords = 5;
+
 template <typename T, int D>
 __host__ __device__ inline size_t warp_region_bytes(int cap) {
   size_t b = (size_t)(D + 1) * cap * sizeof(T) + (size_t)2 * cap * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
-  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) + (kClasses + 1) * sizeof(int) +
-       2 * kClasses * sizeof(uint16_t);
+  b += (size_t)stacks_entries(cap) * sizeof(uint32_t) +
+       (kClasses + 1 + kEvWords) * sizeof(int) + 2 * kClasses * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
   b += kMaxTeam * (sizeof(Moments<T, D>) + sizeof(int));
   return (b + 15) & ~size_t(15);
 }
 
+// per-lane counters of one launch (32 bits suffice for the per-lane counts of
+// sets; the depth sum is a 64-bit particle-level count)
 struct Counters {
-  unsigned long long leaves, depth, splits, degenerate;
+  unsigned leaves, splits, degenerate;
+  unsigned long long depth;
 };
 
 // particle j of the tile, staged at final position gp
@@ -133,6 +144,16 @@ __device__ __forceinline__ void emit_single(const Problem &, const WarpTile<T, D
 }
 
 template <typename T, int D>
+__device__ __forceinline__ void push_rec(const Problem &P, const WarpTile<T, D> &S, int c,
+                                         uint32_t r) {
+  const int slot = atomicAdd(&S.top[c], 1);
+  if (slot < S.stk_cap(c))
+    *S.rec(c, slot) = r;
+  else
+    set_error(P.err, kErrInternal);
+}
+
+template <typename T, int D>
 __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D> &S,
                                            const int32_t *perm, int64_t gb, int b, int m,
                                            int par, Counters &cnt) {
@@ -141,96 +162,105 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
     cnt.leaves += 1;
     return;
   }
-  const int c = size_class(m);
-  const int slot = atomicAdd(&S.top[c], 1);
-  if (slot < S.stk_cap(c))
-    *S.rec(c, slot) = pack_rec(b, m, par);
-  else
-    set_error(P.err, kErrInternal);
+  push_rec<T, D>(P, S, size_class(m), pack_rec(b, m, par));
 }
 
-// one round of class c >= 1 for this warp: kw <= 32/G subsets, G lanes
-// each; rec is the record of the lane's group (read before the round)
-template <typename T, int D, bool VAR>
-__device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                            int64_t gb, int c, int lane, Counters &cnt, int kw, uint32_t rec) {
-  const int lg = c - 1, G = 1 << lg;
-  const int gid = lane >> lg, gl = lane & (G - 1);
-  const bool act = gid < kw;
-  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
+// A rare event of one decision: near-tie bits (kNear*) and rechecks
+// (kRechecked), into the unit's bits and the CTA's counts.
+static __device__ __noinline__ void note_event_words(int *ev, unsigned bits) {
+  atomicOr(reinterpret_cast<unsigned *>(&ev[0]), bits);
+  if (bits & kNearStop) atomicAdd(&ev[1], 1);
+  if (bits & kNearArgmax) atomicAdd(&ev[2], 1);
+  if (bits & kNearCut) atomicAdd(&ev[3], 1);
+  if (bits & kRechecked) atomicAdd(&ev[4], 1);
+}
 
-  // Steps 1-2: moments about the set's first particle
+template <typename T, int D>
+__device__ __forceinline__ void note_event(const WarpTile<T, D> &S, unsigned bits) {
+  note_event_words(S.ev, bits);
+}
+
+// FP32 storage: Steps 2-6 for one set in FP64 from its particles, by the
+// whole warp (warp-uniform call), when an FP32 decision or cut value on it
+// was closer than its error bound.  The cut value is the FP64 centroid
+// rounded down to float; particles in the FP64 near band are cut near-ties.
+template <typename T, int D, bool VAR>
+__device__ void exact_set(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                          int64_t gb, int b, int m, int par, int lane, Counters &cnt) {
+  const unsigned full = 0xffffffffu;
+  const uint16_t *ix = S.idx(par);
+  // the FP64 sums go through this warp's slot of the wide-round scratch
+  // (W, m1[D], m2[D]), one axis at a time, so that few registers are live
+  double *xs = reinterpret_cast<double *>(static_cast<Moments<T, D> *>(S.wide) +
+                                          (threadIdx.x >> 5));
+  const int j0 = ix[b];
   T s[D];
-  {
-    const int j0 = act ? S.idx(par)[b] : 0;
 #pragma unroll
-    for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
-  }
-  Moments<T, D> M;
-  M.zero();
-#pragma unroll 4
-  for (int i = gl; i < m; i += G) {
-    const int j = S.idx(par)[b + i];
-    T q[D];
+  for (int l = 0; l < D; ++l) {
+    s[l] = S.col(l)[j0];
+    const double sl = (double)s[l];
+    double a1 = 0.0, a2 = 0.0, aw = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      const int j = ix[b + i];
+      const double w = (double)S.col(D)[j];
+      const double d = (double)S.col(l)[j] - sl;
+      const double t = w * d;
+      a1 += t;
+      a2 = fma(t, d, a2);
+      if (l == 0) aw += w;
+    }
 #pragma unroll
-    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
-    M.add(S.col(D)[j], q, s);
+    for (int k = 16; k >= 1; k >>= 1) {
+      a1 += __shfl_xor_sync(full, a1, k);
+      a2 += __shfl_xor_sync(full, a2, k);
+      if (l == 0) aw += __shfl_xor_sync(full, aw, k);
+    }
+    if (lane == 0) {
+      xs[1 + l] = a1;
+      xs[1 + D + l] = a2;
+      if (l == 0) xs[0] = aw;
+    }
   }
   __syncwarp();
-  M.group_allreduce(G);
-  // Steps 3-5
-  Cut cut;
-  cut.leaf = 1;
-  cut.k = 0;
-  cut.Q = 0.0;
-  cut.Qt = 0.f;
-  if (act) cut = Decider<T, D, VAR>::run(P, M, s);
-  const bool split = act && !cut.leaf;
-  // Step 6: cut by group-masked ballot scan into the other index buffer
+  double sd[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) sd[l] = (double)s[l];
+  const Cut cut = decide_fp64<D, VAR>(P, xs[0], xs + 1, xs + 1 + D, sd, m);
   const int np = par ^ 1;
-  const T *qk = S.col(cut.k);
-  int cntL = 0, cntR = 0;
-  if (G == 1) {
-    // one lane per set: a serial stable-front / reversed-back partition
-    if (split)
-#pragma unroll 4
-      for (int i = 0; i < m; ++i) {
-        const int j = S.idx(par)[b + i];
-        const int dst = Decider<T, D, VAR>::left(qk[j], cut) ? (b + cntL++) : (b + m - 1 - cntR++);
-        S.idx(np)[dst] = (uint16_t)j;
-      }
-  } else {
-    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
+  int cntL = 0;
+  bool nr = false;
+  if (!cut.leaf) {
+    const T *qk = S.col(cut.k);
     const unsigned lt = lanemask_lt();
-    const int mmax = __reduce_max_sync(0xffffffffu, split ? (unsigned)m : 0u);
-    for (int base = 0; base < mmax; base += G) {
-      const int i = base + gl;
-      const bool valid = split && i < m;
-      const int j = valid ? S.idx(par)[b + i] : 0;
-      const bool lft = valid && Decider<T, D, VAR>::left(qk[j], cut);
-      const unsigned bl = __ballot_sync(0xffffffffu, lft) & gmask;
-      const unsigned br = __ballot_sync(0xffffffffu, valid && !lft) & gmask;
+    int cntR = 0;
+    for (int base = 0; base < m; base += 32) {
+      const int i = base + lane;
+      const bool valid = i < m;
+      const int j = valid ? ix[b + i] : 0;
+      const T q = qk[j];
+      const bool lft = valid && Decider<T, D, VAR>::left(q, cut);
+      nr |= valid && Decider<T, D, VAR>::near(q, cut);
+      const unsigned bl = __ballot_sync(full, lft);
+      const unsigned br = __ballot_sync(full, valid && !lft);
       if (valid) {
-        const int dst =
-            lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
+        const int dst = lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
         S.idx(np)[dst] = (uint16_t)j;
       }
       cntL += __popc(bl);
       cntR += __popc(br);
     }
+    nr = __any_sync(full, nr);
   }
   __syncwarp();
-  const bool degenerate = split && (cntL == 0 || cntR == 0);
-  const bool final_set = act && (cut.leaf || degenerate);
-  const int epar = cut.leaf ? par : np;
-  // final sets: final order and head codes (Step 7 sums them up later)
-  if (final_set) {
+  if (lane == 0) note_event<T, D>(S, kRechecked | cut.near | (nr ? kNearCut : 0u));
+  const bool degenerate = !cut.leaf && (cntL == 0 || cntL == m);
+  if (cut.leaf || degenerate) {
+    const uint16_t *fx = S.idx(cut.leaf ? par : np);
     const int h = head_code(m);
-    for (int i = gl; i < m; i += G)
-      mark_final<T, D>(S, b + i, S.idx(epar)[b + i], i == 0 ? h : 0);
+    for (int i = lane; i < m; i += 32) mark_final<T, D>(S, b + i, fx[b + i], i == 0 ? h : 0);
   }
-  if (gl == 0 && act) {
-    if (final_set) {
+  if (lane == 0) {
+    if (cut.leaf || degenerate) {
       cnt.leaves += 1;
       if (degenerate) cnt.degenerate += 1;
     } else {
@@ -243,6 +273,135 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   __syncwarp();
 }
 
+// the sets of this warp marked in `pend` (a bit at each set's first lane,
+// set ranges broadcast from there), one at a time in FP64 (exact_set)
+template <typename T, int D, bool VAR>
+__device__ __forceinline__ void exact_sets(const Problem &P, const WarpTile<T, D> &S,
+                                           const int32_t *perm, int64_t gb, unsigned pend, int b,
+                                           int m, int par, int lane, Counters &cnt) {
+  const unsigned full = 0xffffffffu;
+  while (pend) {
+    const int src = __ffs(pend) - 1;
+    pend &= pend - 1u;
+    const int bb = __shfl_sync(full, b, src), mm = __shfl_sync(full, m, src),
+              pp = __shfl_sync(full, par, src);
+    exact_set<T, D, VAR>(P, S, perm, gb, bb, mm, pp, lane, cnt);
+  }
+}
+
+// one round of class c >= 1 for this warp: kw <= 32/G subsets, G lanes
+// each; rec is the record of the lane's group (read before the round)
+template <typename T, int D, bool VAR>
+__device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                            int64_t gb, int c, int lane, Counters &cnt, int kw, uint32_t rec) {
+  constexpr bool kF = sizeof(T) == 4;
+  const unsigned full = 0xffffffffu;
+  const int lg = c - 1, G = 1 << lg;
+  const int gid = lane >> lg, gl = lane & (G - 1);
+  const bool act = gid < kw;
+  const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
+  const uint16_t *ix = S.idx(par);
+
+  // Steps 1-2: moments about the set's first particle
+  T s[D];
+  {
+    const int j0 = act ? ix[b] : 0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) s[l] = S.col(l)[j0];
+  }
+  Moments<T, D> M;
+  M.zero();
+#pragma unroll 4
+  for (int i = gl; i < m; i += G) {
+    const int j = ix[b + i];
+    T q[D];
+#pragma unroll
+    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+    M.add(S.col(D)[j], q, s);
+  }
+  __syncwarp();
+  M.group_allreduce(G);
+  // Steps 3-5
+  Cut cut = cut_none();
+  if (act) cut = Decider<T, D, VAR>::run(P, M, s, m, (m + G - 1) >> lg);
+  // FP32 storage: a decision too close to call is taken again in FP64
+  bool redo = kF && cut.unsure;
+  if (cut.near && gl == 0) note_event<T, D>(S, cut.near);
+  const bool split = act && !cut.leaf && !redo;
+  // Step 6: cut by group-masked ballot scan into the other index buffer;
+  // nr: some particle in the cut's near band
+  const int np = par ^ 1;
+  const T *qk = S.col(cut.k);
+  int cntL = 0, cntR = 0;
+  bool nr = false;
+  if (G == 1) {
+    // one lane per set: a serial stable-front / reversed-back partition
+    if (split)
+#pragma unroll 4
+      for (int i = 0; i < m; ++i) {
+        const int j = ix[b + i];
+        const T q = qk[j];
+        nr |= Decider<T, D, VAR>::near(q, cut);
+        const int dst = Decider<T, D, VAR>::left(q, cut) ? (b + cntL++) : (b + m - 1 - cntR++);
+        S.idx(np)[dst] = (uint16_t)j;
+      }
+  } else {
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
+    const unsigned lt = lanemask_lt();
+    const int mmax = __reduce_max_sync(full, split ? (unsigned)m : 0u);
+    for (int base = 0; base < mmax; base += G) {
+      const int i = base + gl;
+      const bool valid = split && i < m;
+      const int j = valid ? ix[b + i] : 0;
+      const T q = qk[j];
+      const bool lft = valid && Decider<T, D, VAR>::left(q, cut);
+      nr |= valid && Decider<T, D, VAR>::near(q, cut);
+      const unsigned bl = __ballot_sync(full, lft) & gmask;
+      const unsigned br = __ballot_sync(full, valid && !lft) & gmask;
+      if (valid) {
+        const int dst =
+            lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
+        S.idx(np)[dst] = (uint16_t)j;
+      }
+      cntL += __popc(bl);
+      cntR += __popc(br);
+    }
+    nr = (__ballot_sync(full, nr) & gmask) != 0u;
+  }
+  __syncwarp();
+  if (nr) {
+    if (kF)
+      redo = true;  // an FP32 cut value too close to a particle: retake in FP64
+    else if (gl == 0)
+      note_event<T, D>(S, kNearCut);
+  }
+  const bool degenerate = split && !redo && (cntL == 0 || cntR == 0);
+  const bool final_set = act && !redo && (cut.leaf || degenerate);
+  const int epar = cut.leaf ? par : np;
+  // final sets: final order and head codes (Step 7 sums them up later)
+  if (final_set) {
+    const int h = head_code(m);
+    for (int i = gl; i < m; i += G)
+      mark_final<T, D>(S, b + i, S.idx(epar)[b + i], i == 0 ? h : 0);
+  }
+  if (gl == 0 && act && !redo) {
+    if (final_set) {
+      cnt.leaves += 1;
+      if (degenerate) cnt.degenerate += 1;
+    } else {
+      cnt.splits += 1;
+      cnt.depth += (unsigned long long)m;
+      push_child<T, D>(P, S, perm, gb, b, cntL, np, cnt);
+      push_child<T, D>(P, S, perm, gb, b + cntL, m - cntL, np, cnt);
+    }
+  }
+  __syncwarp();
+  if (kF) {
+    const unsigned pend = __ballot_sync(full, redo && act && gl == 0);
+    if (pend) exact_sets<T, D, VAR>(P, S, perm, gb, pend, b, m, par, lane, cnt);
+  }
+}
+
 // A wide round: the (up to TEAM/2) pending sets of 193 or more particles,
 // when they would leave warps idle, each get W = TEAM/2^k warps.
 // Moments: each warp sums a strided share, the W partial sums are merged in
@@ -250,12 +409,14 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
 // u-th contiguous segment of the set (32 lanes at a time, conflict-free), a
 // first pass counts its V1 members, and a second writes V1 to the front and
 // V2 to the back of the range at the offsets of the earlier segments, which
-// is the order one warp would write.  Every warp of the team calls this
-// (the idle ones too): it contains CTA barriers.
+// is the order one warp would write.  An FP32 decision or cut too close to
+// call is taken again in FP64 by the group's first warp.  Every warp of the
+// team calls this (the idle ones too): it contains CTA barriers.
 template <typename T, int D, bool VAR, int TEAM>
 __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
                            int64_t gb, int lane, int wt, int sub, int W, bool act, uint32_t rec,
                            Counters &cnt) {
+  constexpr bool kF = sizeof(T) == 4;
   Moments<T, D> *xm = static_cast<Moments<T, D> *>(S.wide);
   int *xc = reinterpret_cast<int *>(xm + kMaxTeam);
   const unsigned full = 0xffffffffu;
@@ -282,17 +443,15 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
   M.warp_allreduce();
   if (lane == 0) xm[wt] = M;
   __syncthreads();
-  Cut cut;
-  cut.leaf = 1;
-  cut.k = 0;
-  cut.Q = 0.0;
-  cut.Qt = 0.f;
+  Cut cut = cut_none();
   if (act) {
     Moments<T, D> Mt = xm[sub * W];
     for (int u = 1; u < W; ++u) Mt.merge(xm[sub * W + u]);
-    cut = Decider<T, D, VAR>::run(P, Mt, s);
+    cut = Decider<T, D, VAR>::run(P, Mt, s, m, (m + 32 * W - 1) / (32 * W));
   }
-  const bool split = act && !cut.leaf;
+  bool redo = kF && cut.unsure;
+  if (cut.near && wl == 0 && lane == 0) note_event<T, D>(S, cut.near);
+  const bool split = act && !cut.leaf && !redo;
   // Step 6: two passes over this warp's segment
   const int np = par ^ 1;
   const T *qk = S.col(cut.k);
@@ -300,18 +459,25 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
   const int s0 = min(m, wl * seg), s1 = min(m, s0 + seg);
   const unsigned lt = lanemask_lt();
   int cl = 0;
+  bool nr = false;
   if (split)
     for (int i0 = s0; i0 < s1; i0 += 32) {
       const int i = i0 + lane;
       const bool valid = i < s1;
-      const bool lft = valid && Decider<T, D, VAR>::left(qk[ix[b + (valid ? i : 0)]], cut);
+      const T q = qk[ix[b + (valid ? i : 0)]];
+      const bool lft = valid && Decider<T, D, VAR>::left(q, cut);
+      nr |= valid && Decider<T, D, VAR>::near(q, cut);
       cl += __popc(__ballot_sync(full, lft));
     }
-  if (lane == 0) xc[wt] = cl;
+  nr = __any_sync(full, nr);
+  if (lane == 0) xc[wt] = cl | (nr ? (1 << 30) : 0);
   __syncthreads();
   int rl = 0, rr = 0, totL = 0;
+  bool gnear = false;
   for (int u = 0; u < W; ++u) {
-    const int cu = act ? xc[sub * W + u] : 0;
+    const int xv = act ? xc[sub * W + u] : 0;
+    const int cu = xv & ((1 << 30) - 1);
+    gnear |= (xv >> 30) != 0;
     const int nu = min(m, (u + 1) * seg) - min(m, u * seg);
     if (u < wl) {
       rl += cu;
@@ -319,7 +485,13 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
     }
     totL += cu;
   }
-  if (split) {
+  if (gnear) {
+    if (kF)
+      redo = true;
+    else if (wl == 0 && lane == 0)
+      note_event<T, D>(S, kNearCut);
+  }
+  if (split && !redo) {
     uint16_t *ox = S.idx(np);
     for (int i0 = s0; i0 < s1; i0 += 32) {
       const int i = i0 + lane;
@@ -337,15 +509,15 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
     }
   }
   __syncthreads();
-  const bool degenerate = split && (totL == 0 || totL == m);
-  const bool final_set = act && (cut.leaf || degenerate);
+  const bool degenerate = split && !redo && (totL == 0 || totL == m);
+  const bool final_set = act && !redo && (cut.leaf || degenerate);
   if (final_set) {
     const uint16_t *fx = S.idx(cut.leaf ? par : np);
     const int h = head_code(m);
     for (int i = wl * 32 + lane; i < m; i += 32 * W)
       mark_final<T, D>(S, b + i, fx[b + i], i == 0 ? h : 0);
   }
-  if (act && wl == 0 && lane == 0) {
+  if (act && !redo && wl == 0 && lane == 0) {
     if (final_set) {
       cnt.leaves += 1;
       if (degenerate) cnt.degenerate += 1;
@@ -356,33 +528,35 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
       push_child<T, D>(P, S, perm, gb, b + totL, m - totL, np, cnt);
     }
   }
+  // redo is the same in every lane of the group's warps
+  if (kF && act && redo && wl == 0) exact_set<T, D, VAR>(P, S, perm, gb, b, m, par, lane, cnt);
 }
 
 // one round of two-particle sets for this warp: kw <= 32 of them, one per
-// lane; rec is the lane's record (read before the round)
+// lane; rec is the lane's record (read before the round).  An FP32 decision
+// or cut too close to call is taken again in FP64 (exact_set).
 template <typename T, int D, bool VAR>
 __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
                            int64_t gb, int lane, Counters &cnt, int kw, uint32_t rec) {
+  constexpr bool kF = sizeof(T) == 4;
   const bool act = lane < kw;
-  if (!act) return;
   const int b = rec_begin(rec), par = rec_par(rec);
-  const int ja = S.idx(par)[b], jb = S.idx(par)[b + 1];
-  T qa[D], qb[D];
+  bool redo = false;
+  if (act) {
+    const int ja = S.idx(par)[b], jb = S.idx(par)[b + 1];
+    T qa[D], qb[D];
 #pragma unroll
-  for (int l = 0; l < D; ++l) {
-    qa[l] = S.col(l)[ja];
-    qb[l] = S.col(l)[jb];
-  }
-  const T wa = S.col(D)[ja], wb = S.col(D)[jb];
-  // the same sums as the general path takes for two particles
-  Moments<T, D> M;
-  M.zero();
-  M.add(wa, qa, qa);
-  M.add(wb, qb, qa);
-  const Cut cut = Decider<T, D, VAR>::run(P, M, qa);
-  bool merged = cut.leaf != 0;
-  int first = ja, second = jb;
-  if (!merged) {
+    for (int l = 0; l < D; ++l) {
+      qa[l] = S.col(l)[ja];
+      qb[l] = S.col(l)[jb];
+    }
+    const T wa = S.col(D)[ja], wb = S.col(D)[jb];
+    // the same sums as the general path takes for two particles
+    Moments<T, D> M;
+    M.zero();
+    M.add(wa, qa, qa);
+    M.add(wb, qb, qa);
+    const Cut cut = Decider<T, D, VAR>::run(P, M, qa, 2, 2);
     T ka = qa[0], kb = qb[0];
 #pragma unroll
     for (int l = 0; l < D; ++l)
@@ -390,25 +564,40 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
         ka = qa[l];
         kb = qb[l];
       }
-    const bool la = Decider<T, D, VAR>::left(ka, cut), lb = Decider<T, D, VAR>::left(kb, cut);
-    if (la == lb) {
-      merged = true;  // degenerate cut: the set stays whole
-      cnt.degenerate += 1;
-    } else if (!la) {
-      first = jb;
-      second = ja;
+    const bool nr = !cut.leaf && !cut.unsure &&
+                    (Decider<T, D, VAR>::near(ka, cut) || Decider<T, D, VAR>::near(kb, cut));
+    redo = kF && (cut.unsure || nr);
+    if (!redo) {
+      const unsigned ev = cut.near | (nr ? kNearCut : 0u);
+      if (ev) note_event<T, D>(S, ev);
+      bool merged = cut.leaf != 0;
+      int first = ja, second = jb;
+      if (!merged) {
+        const bool la = Decider<T, D, VAR>::left(ka, cut), lb = Decider<T, D, VAR>::left(kb, cut);
+        if (la == lb) {
+          merged = true;  // degenerate cut: the set stays whole
+          cnt.degenerate += 1;
+        } else if (!la) {
+          first = jb;
+          second = ja;
+        }
+      }
+      if (merged) {
+        mark_final<T, D>(S, b, first, kHeadMerged);
+        mark_final<T, D>(S, b + 1, second, 0);
+        cnt.leaves += 1;
+      } else {
+        mark_final<T, D>(S, b, first, kHeadSingle);
+        mark_final<T, D>(S, b + 1, second, kHeadSingle);
+        cnt.leaves += 2;
+        cnt.splits += 1;
+        cnt.depth += 2;
+      }
     }
   }
-  if (merged) {
-    mark_final<T, D>(S, b, first, kHeadMerged);
-    mark_final<T, D>(S, b + 1, second, 0);
-    cnt.leaves += 1;
-  } else {
-    mark_final<T, D>(S, b, first, kHeadSingle);
-    mark_final<T, D>(S, b + 1, second, kHeadSingle);
-    cnt.leaves += 2;
-    cnt.splits += 1;
-    cnt.depth += 2;
+  if (kF) {
+    const unsigned pend = __ballot_sync(0xffffffffu, redo);
+    if (pend) exact_sets<T, D, VAR>(P, S, perm, gb, pend, b, 2, par, lane, cnt);
   }
 }
 
@@ -425,19 +614,21 @@ struct UnitSource {
   int mode;
 };
 
-// one unit: first sorted position, size, depth of its root
+// one unit: first sorted position, size, depth of its root, cell id
 __device__ __forceinline__ void unit_at(const Problem &P, const UnitSource &U, int t, int64_t &gb,
-                                        int &n, int &depth0) {
+                                        int &n, int &depth0, int &cell) {
   if (U.mode == 2) {
     const int4 pc = P.pieces[t];
     gb = pc.x;
     n = pc.y - pc.x;
     depth0 = pc.z;
+    cell = pc.w;
   } else {
     const int c = U.list[t];
     gb = P.cell_begin[c];
     n = P.cell_begin[c + 1] - (int)gb;
     depth0 = 0;
+    cell = c;
   }
 }
 
@@ -456,6 +647,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int count = *U.count;
   if (count == 0) return;  // an empty class: leave before any other work
+  if (timed_out(P.err)) return;
   const int lane = threadIdx.x & 31, wt = threadIdx.x >> 5, tt = threadIdx.x;
   constexpr int kThreads = 32 * TEAM;
   WarpTile<T, D> S;
@@ -470,7 +662,8 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     S.stk0 = reinterpret_cast<uint32_t *>(base + off);
     S.top = reinterpret_cast<int *>(S.stk0 + stacks_entries(cap));
     ctl = S.top + kClasses;
-    S.soff = reinterpret_cast<uint16_t *>(ctl + 1);
+    S.ev = ctl + 1;
+    S.soff = reinterpret_cast<uint16_t *>(ctl + 1 + kEvWords);
     {
       const size_t woff =
           ((size_t)(reinterpret_cast<unsigned char *>(S.soff + 2 * kClasses) - base) + 15) &
@@ -484,10 +677,11 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       S.soff[tt] = (uint16_t)(tt == 0 ? 0 : o);
       S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap);
     }
+    if (tt < kEvWords) S.ev[tt] = 0;
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
   const int chunk = (U.mode == 0 || U.mode == 3) ? kWarpChunk : 1;
-  Counters cnt{0ull, 0ull, 0ull, 0ull};
+  Counters cnt{0u, 0u, 0u, 0ull};
   unsigned long long merged = 0, passed = 0;
 
   for (;;) {
@@ -503,8 +697,8 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     const int c1 = min(c0 + chunk, count);
     for (int t = c0; t < c1; ++t) {
       int64_t gb;
-      int n, depth0;
-      unit_at(P, U, t, gb, n, depth0);
+      int n, depth0, cell;
+      unit_at(P, U, t, gb, n, depth0, cell);
       if (U.mode != 2 && (n <= P.n_min || n == 1)) {
         // Sec. 3 "Input": cells with at most N_min particles are not merged
         for (int i = tt; i < n; i += kThreads) {
@@ -528,8 +722,8 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       if (t + 1 < c1 && !perm && tt < D + 1) {
         // the next unit of this chunk: pull its columns into L2 meanwhile
         int64_t nb;
-        int nn, nd;
-        unit_at(P, U, t + 1, nb, nn, nd);
+        int nn, nd, nc;
+        unit_at(P, U, t + 1, nb, nn, nd, nc);
         const int64_t ne = nb + nn;
         const size_t es = sizeof(T);
         const char *col = static_cast<const char *>(tt < D ? P.q[tt] : P.w);
@@ -633,7 +827,20 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         stage<T, D>(P, S, gb + i, j);
       }
       __syncthreads();
+      if (tt == 0 && S.ev[0] != 0) {
+        // the unit's near-tie bits, into its cell's word
+        const unsigned f = (unsigned)S.ev[0];
+        S.ev[0] = 0;
+        if (atomicOr(&P.cell_flags[cell], f) == 0u)
+          atomicAdd(&P.stats[kStCellsFlagged], 1ull);
+      }
     }
+  }
+  if (tt == 0) {
+    const int kinds[4] = {kStNearStop, kStNearArgmax, kStNearCut, kStRecheck};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (S.ev[1 + k]) atomicAdd(&P.stats[kinds[k]], (unsigned long long)S.ev[1 + k]);
   }
 #pragma unroll
   for (int m = 16; m >= 1; m >>= 1) {
@@ -643,10 +850,10 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     cnt.degenerate += __shfl_xor_sync(0xffffffffu, cnt.degenerate, m);
   }
   if (lane == 0) {
-    if (cnt.leaves) atomicAdd(&P.stats[kStLeaves], cnt.leaves);
+    if (cnt.leaves) atomicAdd(&P.stats[kStLeaves], (unsigned long long)cnt.leaves);
     if (cnt.depth) atomicAdd(&P.stats[kStDepth], cnt.depth);
-    if (cnt.splits) atomicAdd(&P.stats[kStSplits], cnt.splits);
-    if (cnt.degenerate) atomicAdd(&P.stats[kStDegenerate], cnt.degenerate);
+    if (cnt.splits) atomicAdd(&P.stats[kStSplits], (unsigned long long)cnt.splits);
+    if (cnt.degenerate) atomicAdd(&P.stats[kStDegenerate], (unsigned long long)cnt.degenerate);
     if (wt == 0 && merged) atomicAdd(&P.stats[kStCellsMerged], merged);
     if (wt == 0 && passed) atomicAdd(&P.stats[kStCellsPass], passed);
   }

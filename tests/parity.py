@@ -3,11 +3,17 @@ and compare it with the CPU oracle on the same seeded inputs.
 
 Comparison rules:
 * membership: per cell, the local output index of every particle and the
-  number of outputs must be identical, except in cells where the oracle
-  flagged a near-tie (a decision within 1e-9 relative of a threshold, of the
-  runner-up axis, or a particle within rounding of the cut value);
+  number of outputs must be identical, except in cells where the oracle or
+  the CUDA path flagged a near-tie (a decision within about 1e-9 relative of
+  a threshold or of the runner-up axis, or a particle within rounding of the
+  cut value).  This holds for both precisions: the mixed path certifies each
+  FP32 decision against its error bound and retakes the close ones in FP64;
 * coordinates (FP64 path): |gpu - oracle| <= 1e-10 * scale, scale the mean
-  |q| of the cell on that axis (weights: 1e-10 relative);
+  |q| of that axis (weights: 1e-10 relative);
+* coordinates (mixed path, FP32 positions out, FP64 W and P): the position
+  within one float ulp of the oracle's FP64 centroid (plus 1e-12 * scale);
+  W within 1e-12 relative and P within 1e-12 * scale: both are FP64 sums of
+  exact products of the stored float values;
 * conservation: per cell, |sum_out w - sum_in w| <= 1e-12 sum_in w and
   |sum_out w p - sum_in w p| <= 1e-12 sum_in w |p| on every momentum axis.
 """
@@ -40,6 +46,7 @@ def run_gpu(p, precision="fp64", tol_x=None, tol_p=None, n_min=None, capacity=No
                w=out.w[:M].cpu().numpy(),
                index=out.index[:n].cpu().numpy(),
                count_dev=int(out.count_dev.item()),
+               flags=out.cell_flags.cpu().numpy().astype(np.uint32),
                stats=m.stats())
     if merger is None:
         m.close()
@@ -53,10 +60,18 @@ def local_index(index, cell_of_input, out_cell, n_cells):
     return index.astype(np.int64) - first[cell_of_input]
 
 
-def compare(p, g, r, coord_rtol=1e-10, check_coords=True, allow_flagged=True):
+def flagged_cells(g, r, n_cells):
+    """Cells with a near-tie flag from the oracle or from the CUDA path."""
+    f = r.flags != 0
+    if g.get("flags") is not None:
+        f = f | ((g["flags"][:n_cells] & binding.PMA_NEAR_ANY) != 0)
+    return f
+
+
+def compare(p, g, r, coord_rtol=1e-10, check_coords=True, allow_flagged=True, mixed=False):
     """Assert GPU result g (dict) equals oracle result r; returns a report."""
     n_cells = p.n_cells
-    flagged = r.flags != 0 if allow_flagged else np.zeros(n_cells, bool)
+    flagged = flagged_cells(g, r, n_cells) if allow_flagged else np.zeros(n_cells, bool)
     gi = local_index(g["index"], p.cell, g["cell"], n_cells)
     oi = local_index(r.index, p.cell, r.cell, n_cells)
     g_cnt = np.bincount(g["cell"], minlength=n_cells)
@@ -71,7 +86,7 @@ def compare(p, g, r, coord_rtol=1e-10, check_coords=True, allow_flagged=True):
                   unexplained=int(unexplained.sum()), M_gpu=g["count"], M_oracle=r.count)
     assert not unexplained.any(), "membership differs in unflagged cells: %s" % (
         np.flatnonzero(unexplained)[:10],)
-    if not flagged.any():
+    if not bad_cells.any():
         assert g["count"] == r.count
         np.testing.assert_array_equal(g["index"], r.index)
         np.testing.assert_array_equal(g["cell"], r.cell)
@@ -79,12 +94,30 @@ def compare(p, g, r, coord_rtol=1e-10, check_coords=True, allow_flagged=True):
         ok_out = ~np.isin(g["cell"], np.flatnonzero(bad_cells))
         ok_ref = ~np.isin(r.cell, np.flatnonzero(bad_cells))
         assert ok_out.sum() == ok_ref.sum()
-        np.testing.assert_allclose(g["w"][ok_out], r.w[ok_ref], rtol=coord_rtol, atol=0)
-        for arr, ref, q in ((g["pos"], r.pos, p.pos), (g["mom"], r.mom, p.mom)):
-            for a in range(arr.shape[0]):
-                scale = float(np.mean(np.abs(q[a]))) if q.shape[1] else 1.0
-                np.testing.assert_allclose(arr[a][ok_out], ref[a][ok_ref], rtol=0,
-                                           atol=coord_rtol * max(scale, 1e-300))
+        w_rtol = 1e-12 if mixed else coord_rtol
+        np.testing.assert_allclose(g["w"][ok_out], r.w[ok_ref], rtol=w_rtol, atol=0)
+        for a in range(g["pos"].shape[0]):
+            scale = float(np.mean(np.abs(p.pos[a]))) if p.pos.shape[1] else 1.0
+            got, ref = g["pos"][a][ok_out], r.pos[a][ok_ref]
+            if mixed:
+                # float output: the FP64 centroid rounded to nearest float
+                tol = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64) \
+                    + 1e-12 * max(scale, 1e-300)
+                bad = np.abs(got - ref) > tol
+                assert not bad.any(), ("position axis", a, got[bad][:5], ref[bad][:5])
+            else:
+                np.testing.assert_allclose(got, ref, rtol=0, atol=coord_rtol * max(scale, 1e-300))
+        for a in range(g["mom"].shape[0]):
+            scale = float(np.mean(np.abs(p.mom[a]))) if p.mom.shape[1] else 1.0
+            got, ref = g["mom"][a][ok_out], r.mom[a][ok_ref]
+            if mixed:
+                # an FP64 mean of exact products: 1e-12 of the larger of the
+                # axis scale and the value itself
+                tol = 1e-12 * np.maximum(max(scale, 1e-300), np.abs(ref))
+                bad = np.abs(got - ref) > tol
+                assert not bad.any(), ("momentum axis", a, got[bad][:5], ref[bad][:5])
+            else:
+                np.testing.assert_allclose(got, ref, rtol=0, atol=coord_rtol * max(scale, 1e-300))
     return report
 
 

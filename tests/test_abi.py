@@ -63,3 +63,26 @@ def test_null_handle_calls_are_rejected():
     assert lib.pma_sync(None) == binding.PMA_ERR_INVALID_ARG
     assert lib.pma_destroy(None) == binding.PMA_OK
     assert lib.pma_last_error(None) == b""
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the ctypes mirrors of pma_config, pma_output and pma_stats have the C
+    # layout: sizes and field offsets from a C program compiled against pma.h
+    import subprocess
+    structs = {"pma_config": binding.pma_config, "pma_output": binding.pma_output,
+               "pma_stats": binding.pma_stats}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pma.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, f)]) == getattr(cls, f).offset, (name, f)

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from paper_1504_00636_gb300 import binding, synth
 
-from parity import compare, conservation, local_index, run_gpu
+from parity import compare, conservation, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -41,11 +41,8 @@ def test_mixed_variant_matches_oracle_on_rounded_inputs(make, flags, variant):
     tx, tp = 0.3, 0.05
     g = run_gpu(p, "mixed", tol_x=tx, tol_p=tp, flags=flags)
     r = oracle.merge_particles(p, threads=8, tol_x=tx, tol_p=tp, variant=variant)
-    gi = local_index(g["index"], p.cell, g["cell"], p.n_cells)
-    oi = local_index(r.index, p.cell, r.cell, p.n_cells)
-    diff = np.unique(p.cell[gi != oi])
-    unexplained = [c for c in diff if not r.flags[c]]
-    assert len(unexplained) <= max(1, 0.01 * np.unique(p.cell).size), unexplained[:10]
+    rep = compare(p, g, r, mixed=True)
+    assert rep["unexplained"] == 0
     conservation(p, g)
 
 
