@@ -222,7 +222,8 @@ constexpr unsigned kNearArgmax = 2u;
 constexpr unsigned kNearCut = 4u;
 constexpr unsigned kRechecked = 8u;
 // FP64 near-tie threshold on squared CVs (|Delta^2 - T^2| <= 4e-9 T^2 covers
-// |Delta - T| <= 1e-9 T with room for the rounding of either side)
+// |Delta - T| <= 1e-9 T with room for the rounding of either side); the stop
+// test uses the exponent-field test near_rel28, at 2^-28 to 2^-27 relative
 constexpr double kNearRel2 = 4e-9;
 
 struct Cut {
@@ -248,12 +249,40 @@ __device__ __forceinline__ Cut cut_none() {
   return c;
 }
 
+// Approximate MUFU square root and reciprocal (relative error below 2^-21);
+// used only inside error bounds, which carry a safety factor for them.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// |a - b| <= 2^-28 |b| (up to a factor 2), from the exponent fields alone
+// (no FP64 arithmetic): the near-tie test of an FP64 comparison
+__device__ __forceinline__ bool near_rel28(double diff, double b) {
+  const int ed = (__double2hiint(diff) >> 20) & 0x7ff, eb = (__double2hiint(b) >> 20) & 0x7ff;
+  return ed <= eb - 28;
+}
+
 // Steps 3-5 in FP64 from moment values (W, m1, m2 about the shift s) of a
 // subset of m particles.  VAR = false: the paper's rule only; true: the
 // variants in P.variant.  Near-tie bits: some |Delta_l^2 - T_l^2| within
-// kNearRel2 T_l^2 (stop), the runner-up axis within kNearRel2 of the chosen
-// one (argmax).  The cut band is 64 m eps (|s_k| + sqrt(m2_k / W)), which is
+// about 2^-28 T_l^2 (stop), the runner-up axis within kNearRel2 of the
+// chosen one (argmax).  The cut band is 64 m eps (|s_k| + sqrt(m2_k / W)), which is
 // at least 64 m eps (sum w |q_k|) / W by Cauchy-Schwarz.
+// The constants of the FP64 decision in a small struct (same member names as
+// in Problem) that an out-of-line path can read from shared memory.
+struct DecideConsts {
+  double tol2_x, tol2_p;
+  double L2[3];
+  int32_t dx, variant;
+};
+
 template <int D, bool VAR = true, class PP = Problem>
 __device__ __forceinline__ Cut decide_fp64(const PP &P, double W, const double *m1,
                                            const double *m2, const double *s, int m) {
@@ -286,7 +315,7 @@ __device__ __forceinline__ Cut decide_fp64(const PP &P, double W, const double *
     // Delta_l <= T  <=>  V <= T^2 den  (den = 0: only V = 0 passes)
     const double t = tol2 * den;
     if (!(V <= t)) c.leaf = 0;
-    if (t > 0.0 && fabs(V - t) <= kNearRel2 * t) c.near |= kNearStop;
+    if (t > 0.0 && near_rel28(V - t, t)) c.near |= kNearStop;
     // first maximum of V / kden = Delta_l^2, or (Delta_l / T_l)^2 for the
     // normalised variant; kden = 0 is +infinity, and V = 0 counts as 0
     double kden = normd ? t : den;
@@ -343,6 +372,9 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
                                             const float *s, int run) {
   constexpr float u = 1.0f / (1 << 24);
   const float kk = (float)(run + 8) * (2.0f * u);
+  // |V - V_exact| <= cV (a + b): W m2 and m1^2 are off by 2 kk a and by
+  // 2 |m1| kk sqrt(a) + ... <= kk (a + b) (AM-GM), plus the roundings
+  const float cV = (3.f * kk + 10.f * u) * 1.0625f;
   const float inf = __int_as_float(0x7f800000);
   const float W = M.W.val();
   const float eW = kk * W;
@@ -356,11 +388,11 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
     for (int l = 0; l < D; ++l)
       if (l >= P.dx) {
         const float m1 = M.m1[l].val(), m2 = fmaxf(M.m2[l].val(), 0.f);
-        const float em1 = kk * sqrtf(W * m2) + u * fabsf(m1);
+        const float sa = sqrt_approx(W * m2) * 1.0001f;
         const float Pw = fmaf(s[l], W, m1);
-        const float eP = fabsf(s[l]) * eW + em1 + 2.f * u * (fabsf(s[l] * W) + fabsf(m1));
+        const float eP = kk * (fabsf(s[l]) * W + sa) + 3.f * u * (fabsf(s[l] * W) + fabsf(m1));
         denN = fmaf(Pw, Pw, denN);
-        eDN += 2.f * fabsf(Pw) * eP + eP * eP;
+        eDN = fmaf(2.f * fabsf(Pw) + eP, eP, eDN);
       }
     eDN = (eDN + 8.f * u * denN) * 1.0625f;
   }
@@ -373,13 +405,11 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
     const float m1 = M.m1[l].val(), m2 = fmaxf(M.m2[l].val(), 0.f);
     const float a = m2 * W, b = m1 * m1;
     const float V = fmaxf(a - b, 0.f);
-    const float em1 = kk * sqrtf(a) + u * fabsf(m1);
-    const float eV =
-        (2.f * kk * a + 2.f * fabsf(m1) * em1 + em1 * em1 + 4.f * u * (a + b)) * 1.0625f;
+    const float eV = cV * (a + b);
     float den, eD, tol2;
     if (l < P.dx) {
       den = P.L2f[l] * (W * W);
-      eD = (2.f * kk + 4.f * u) * den * 1.0625f;
+      eD = (2.f * kk + 4.f * u) * 1.0625f * den;
       tol2 = P.tol2_xf;
     } else if (pnorm) {
       den = denN;
@@ -387,24 +417,37 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
       tol2 = P.tol2_pf;
     } else {
       const float Pw = fmaf(s[l], W, m1);
-      const float eP = fabsf(s[l]) * eW + em1 + 2.f * u * (fabsf(s[l] * W) + fabsf(m1));
+      const float sa = sqrt_approx(a) * 1.0001f;  // >= sum w |q - s|
+      const float eP = kk * (fabsf(s[l]) * W + sa) + 3.f * u * (fabsf(s[l] * W) + fabsf(m1));
       den = Pw * Pw;
-      eD = (2.f * fabsf(Pw) * eP + eP * eP + 2.f * u * den) * 1.0625f;
+      eD = (fmaf(2.f * fabsf(Pw) + eP, eP, 2.f * u * den)) * 1.0625f;
       tol2 = P.tol2_pf;
     }
     // Step 3: Delta_l <= T  <=>  V <= T^2 den
     const float t = tol2 * den;
     const float f = V - t;
     if (f > 0.f) c.leaf = 0;
-    if (!(fabsf(f) > eV + tol2 * eD + 2.f * u * (V + t))) sure = false;
-    // Step 4: score V / kden (Delta^2, or (Delta / T)^2 normalised)
+    if (!(fabsf(f) > fmaf(tol2, eD, eV) + 2.f * u * (V + t))) sure = false;
+    // relative bounds need the sums away from the ends of the FP32 range
+    // (a tiny a + b may be an underflowed spread): FP64 decides there
+    if (!(a + b >= 1e-24f) || !(a + b <= 1e30f) || !(den <= 1e30f) || (den != 0.f && den < 1e-30f))
+      sure = false;
+    // Step 4: score V / kden (Delta^2, or (Delta / T)^2 normalised) with
+    // bounds: 1 / (k + e) >= (1 - e / k) / k and 1 / (k - e) <= (1 + 2 e / k) / k
+    // for e <= k / 2
     const float kden = normd ? t : den, eK = normd ? tol2 * eD : eD;
-    const float r = V == 0.f ? 0.f : (kden > 0.f ? __fdividef(V, kden) : inf);
-    const float lo =
-        V > eV ? (kden + eK > 0.f ? __fdividef(V - eV, kden + eK) * (1.f - 8.f * u) : inf) : 0.f;
-    const float hi = (V + eV == 0.f)
-                         ? 0.f
-                         : (kden > eK ? __fdividef(V + eV, kden - eK) * (1.f + 8.f * u) : inf);
+    const float rk = rcp_approx(kden);
+    const float rho = eK * rk * 1.0001f + 4.f * u;
+    float r, lo, hi;
+    if (kden > 0.f && rho < 0.5f) {
+      r = V * rk;
+      lo = V > eV ? (V - eV) * rk * (1.f - rho - 8.f * u) : 0.f;
+      hi = (V + eV) * rk * (1.f + 2.f * rho + 8.f * u);
+    } else {
+      r = V == 0.f ? 0.f : (kden > 0.f ? V * rk : inf);
+      lo = (V > eV && eK == 0.f && kden == 0.f) ? inf : 0.f;
+      hi = (V + eV == 0.f) ? 0.f : inf;
+    }
     if (r > best) {
       otherHi = fmaxf(otherHi, bestHi);
       best = r;
@@ -422,7 +465,7 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
     return c;
   }
   if (c.leaf) return c;
-  // cut value Q = s_k + m1_k / W as a double-float, then rounded down
+  // cut value Q = s_k + m1_k / W as a double-float Qh + Ql
   float sk = s[0], m1h = M.m1[0].hi(), m1l = M.m1[0].lo(), m2k = M.m2[0].val();
 #pragma unroll
   for (int l = 0; l < D; ++l)
@@ -432,12 +475,14 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
       m1l = M.m1[l].lo();
       m2k = M.m2[l].val();
     }
-  float Wh = M.W.hi(), Wl = M.W.lo();
-  float q0 = __fdiv_rn(m1h, Wh);
-  float p = q0 * Wh;
-  float pe = fmaf(q0, Wh, -p);
-  float rr = ((m1h - p) - pe) + m1l - q0 * Wl;
-  float q1 = rr / Wh;
+  // any approximation q0 of m1h / Wh serves: the exact remainder
+  // m1h - q0 Wh gives the correction q1
+  const float Wh = M.W.hi(), Wl = M.W.lo(), rW = rcp_approx(Wh);
+  const float q0 = m1h * rW;
+  const float p = q0 * Wh;
+  const float pe = fmaf(q0, Wh, -p);
+  const float rr = ((m1h - p) - pe) + m1l - q0 * Wl;
+  const float q1 = rr * rW;
   // (h, e) = TwoSum(sk, q0)
   float h = __fadd_rn(sk, q0);
   float bp = __fsub_rn(h, sk);
@@ -448,12 +493,103 @@ __device__ __forceinline__ Cut decide_mixed(const Problem &P, const Moments<floa
   c.Qt = (Ql < 0.f) ? __int_as_float(__float_as_int(Qh) - (Qh > 0.f ? 1 : (Qh < 0.f ? -1 : 0)))
                     : Qh;
   if (Qh == 0.f && Ql < 0.f) c.Qt = -__int_as_float(1);  // largest float below zero
-  // |Q - Q_exact| <= (e_m1 + |m1 / W| e_W) / W, plus the double-float's own
-  // rounding and the rounding of this bound
-  const float em1k = kk * sqrtf(fmaxf(m2k, 0.f) * W) + u * fabsf(m1h);
-  const float eQ = (em1k + fabsf(q0) * eW) / W * 1.0625f + 4.f * u * fabsf(Qh) + 1e-37f;
-  c.Qlo_f = __fsub_rd(Qh, eQ);
-  c.Qhi_f = __fadd_ru(Qh, eQ);
+  // |Qh + Ql - Q_exact| <= eQ = (e_m1 + |m1 / W| e_W) / W plus the
+  // double-float's own rounding.  A float q is on the same side of Qh + Ql as
+  // of Q_exact unless it lies within eQ of Qh + Ql: the band [Qlo_f, Qhi_f]
+  // holds those floats (it is empty when no float is that close).
+  const float em1k = kk * sqrt_approx(fmaxf(m2k, 0.f) * W) * 1.0001f + u * fabsf(m1h);
+  const float eQ = (em1k + fabsf(q0) * eW) * rW * 1.0625f + 4.f * u * fabsf(q1) +
+                   16.f * u * u * (fabsf(sk) + fabsf(q0)) + 1e-37f;
+  c.Qlo_f = __fadd_ru(Qh, __fsub_rd(Ql, eQ));
+  c.Qhi_f = __fadd_rd(Qh, __fadd_ru(Ql, eQ));
+  return c;
+}
+
+// Steps 3-4 for a set of two float particles a, b (weights wa, wb), with a
+// certificate, as decide_mixed: W^2 var_l = wa wb d_l^2 (d = q_b - q_a) and
+// W P_l = wa q_a + wb q_b carry relative errors of a few u, so the bounds are
+// simple.  The cut needs no value: the exact centroid lies strictly between
+// two distinct values, so the smaller goes to V1.  unsure = 1 hands the pair
+// to the FP64 recheck.
+template <int D, bool VAR = true>
+__device__ __forceinline__ Cut decide_pair(const Problem &P, float wa, float wb, const float *qa,
+                                           const float *qb) {
+  constexpr float u = 1.0f / (1 << 24);
+  const float inf = __int_as_float(0x7f800000);
+  const bool normd = VAR && (P.variant & kVarNormalized) != 0;
+  const bool pnorm = VAR && (P.variant & kVarPNorm) != 0;
+  Cut c = cut_none();
+  const float W = wa + wb, ww = wa * wb;
+  float denN = 0.f, eDN = 0.f;
+  if (pnorm) {
+#pragma unroll
+    for (int l = 0; l < D; ++l)
+      if (l >= P.dx) {
+        const float Pw = fmaf(wa, qa[l], wb * qb[l]);
+        const float eP = 3.f * u * (fabsf(wa * qa[l]) + fabsf(wb * qb[l]));
+        denN = fmaf(Pw, Pw, denN);
+        eDN = fmaf(2.f * fabsf(Pw) + eP, eP, eDN);
+      }
+    eDN = (eDN + 8.f * u * denN) * 1.0625f;
+  }
+  bool sure = true;
+  float best = -1.f, bestLo = 0.f, bestHi = 0.f, otherHi = 0.f;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const float d = qb[l] - qa[l];
+    const float V = ww * (d * d);
+    const float eV = 8.f * u * V;
+    // an underflowed or overflowed V: FP64 decides
+    if ((d != 0.f && !(V >= 1e-30f)) || !(V <= 1e30f)) sure = false;
+    float den, eD, tol2;
+    if (l < P.dx) {
+      den = P.L2f[l] * (W * W);
+      eD = 8.f * u * den;
+      tol2 = P.tol2_xf;
+    } else if (pnorm) {
+      den = denN;
+      eD = eDN;
+      tol2 = P.tol2_pf;
+    } else {
+      const float Pw = fmaf(wa, qa[l], wb * qb[l]);
+      const float eP = 3.f * u * (fabsf(wa * qa[l]) + fabsf(wb * qb[l]));
+      den = Pw * Pw;
+      eD = (fmaf(2.f * fabsf(Pw) + eP, eP, 2.f * u * den)) * 1.0625f;
+      tol2 = P.tol2_pf;
+    }
+    if (!(den <= 1e30f) || (den != 0.f && den < 1e-30f)) sure = false;
+    const float t = tol2 * den;
+    const float f = V - t;
+    if (f > 0.f) c.leaf = 0;
+    if (!(fabsf(f) > fmaf(tol2, eD, eV) + 2.f * u * (V + t))) sure = false;
+    const float kden = normd ? t : den, eK = normd ? tol2 * eD : eD;
+    const float rk = rcp_approx(kden);
+    const float rho = eK * rk * 1.0001f + 4.f * u;
+    float r, lo, hi;
+    if (kden > 0.f && rho < 0.5f) {
+      r = V * rk;
+      lo = V > eV ? (V - eV) * rk * (1.f - rho - 8.f * u) : 0.f;
+      hi = (V + eV) * rk * (1.f + 2.f * rho + 8.f * u);
+    } else {
+      r = V == 0.f ? 0.f : (kden > 0.f ? V * rk : inf);
+      lo = (V > eV && eK == 0.f && kden == 0.f) ? inf : 0.f;
+      hi = (V + eV == 0.f) ? 0.f : inf;
+    }
+    if (r > best) {
+      otherHi = fmaxf(otherHi, bestHi);
+      best = r;
+      bestLo = lo;
+      bestHi = hi;
+      c.k = l;
+    } else {
+      otherHi = fmaxf(otherHi, hi);
+    }
+  }
+  if (!c.leaf && !(bestLo > otherHi)) sure = false;
+  if (!sure) {
+    c.unsure = 1;
+    c.leaf = 0;
+  }
   return c;
 }
 

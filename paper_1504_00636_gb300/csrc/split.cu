@@ -306,18 +306,28 @@ __device__ Moments<A, D> block_moments(const Problem &P, const int32_t *perm, in
   A sa[D];
 #pragma unroll
   for (int l = 0; l < D; ++l) sa[l] = (A)s[l];
-  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
-    int src = perm[i];
-    A q[D];
+  // runs of at most kBigRun terms per thread, folded exactly into M (the
+  // error bound of FP32 sums grows with the run length)
+  constexpr int kBigRun = 32;
+  const int64_t step = blockDim.x;
+  for (int64_t blk = b + threadIdx.x; blk < e; blk += step * kBigRun) {
+    Moments<A, D> R;
+    R.zero();
+    const int64_t end = min(e, blk + step * kBigRun);
+    for (int64_t i = blk; i < end; i += step) {
+      int src = perm[i];
+      A q[D];
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-      const T x = StoreOf<T>::load(P.q[l], src);
-      bad |= !finite_val(x);
-      q[l] = (A)x;
+      for (int l = 0; l < D; ++l) {
+        const T x = StoreOf<T>::load(P.q[l], src);
+        bad |= !finite_val(x);
+        q[l] = (A)x;
+      }
+      T w = StoreOf<T>::load(P.w, src);
+      bad |= !(w > T(0)) || !finite_val(w);
+      R.add((A)w, q, sa);
     }
-    T w = StoreOf<T>::load(P.w, src);
-    bad |= !(w > T(0)) || !finite_val(w);
-    M.add((A)w, q, sa);
+    M.merge(R);
   }
   M.warp_allreduce();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -381,7 +391,8 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
           cut = decide_exact<T, D, true>(P, M, s, mset);
         } else {
           Moments<T, D> M = block_moments<T, T, D>(P, P.perm, b, e, s, sh, bad);
-          cut = Decider<T, D>::run(P, M, s, mset, (int)((e - b + blockDim.x - 1) / blockDim.x));
+          const int64_t run = (e - b + blockDim.x - 1) / blockDim.x;
+          cut = Decider<T, D>::run(P, M, s, mset, run < 32 ? (int)run : 32);
         }
         if (bad) set_error(P.err, kErrInput);
         if (cut.unsure) {

@@ -50,9 +50,23 @@ struct Decider<double, D, VAR> {
     }
     return decide_fp64<D, VAR>(P, M.W.v, m1, m2, s, m);
   }
-  __device__ static __forceinline__ bool left(double q, const Cut &c) { return q <= c.Q; }
+  // order-preserving integer keys of doubles: the cut compares run on the
+  // integer pipes, off the (slow) FP64 pipe.  The key order equals the
+  // numeric order except that -0 < +0, so the cut value's -0 becomes +0.
+  __device__ static __forceinline__ unsigned long long key(double x) {
+    const long long b = __double_as_longlong(x);
+    return (unsigned long long)(b ^ ((b >> 63) | (long long)0x8000000000000000ull));
+  }
+  __device__ static __forceinline__ unsigned long long key_cut(double Q) {
+    const long long b = __double_as_longlong(Q);
+    return b == (long long)0x8000000000000000ull ? 0x8000000000000000ull : key(Q);
+  }
+  __device__ static __forceinline__ bool left(double q, const Cut &c) {
+    return key(q) <= key_cut(c.Q);
+  }
   __device__ static __forceinline__ bool near(double q, const Cut &c) {
-    return q >= c.Qlo && q <= c.Qhi;
+    const unsigned long long k = key(q);
+    return k >= key(c.Qlo) && k <= key(c.Qhi);
   }
 };
 

@@ -85,6 +85,7 @@ struct WarpTile {
                    // of the region shared with class 0), [kClasses] capacities
   int *ev;         // [kEvWords]: near-tie bits of the current unit, then the
                    // CTA's counts of near-ties by kind and of FP64 rechecks
+  const DecideConsts *dk;  // the FP64 decision's constants (for rechecks)
   void *wide;      // wide rounds: [kMaxTeam] partial moments, [kMaxTeam] counts
   int cap;
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
@@ -109,6 +110,8 @@ __host__ __device__ inline size_t warp_region_bytes(int cap) {
        (kClasses + 1 + kEvWords) * sizeof(int) + 2 * kClasses * sizeof(uint16_t);
   b = (b + 15) & ~size_t(15);
   b += kMaxTeam * (sizeof(Moments<T, D>) + sizeof(int));
+  b = (b + 15) & ~size_t(15);
+  b += sizeof(DecideConsts);
   return (b + 15) & ~size_t(15);
 }
 
@@ -144,25 +147,33 @@ __device__ __forceinline__ void emit_single(const Problem &, const WarpTile<T, D
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void push_rec(const Problem &P, const WarpTile<T, D> &S, int c,
+__device__ __forceinline__ void push_rec(unsigned *err, const WarpTile<T, D> &S, int c,
                                          uint32_t r) {
   const int slot = atomicAdd(&S.top[c], 1);
   if (slot < S.stk_cap(c))
     *S.rec(c, slot) = r;
   else
-    set_error(P.err, kErrInternal);
+    set_error(err, kErrInternal);
+}
+
+// a child set of m particles at [b, b + m) of index buffer par: a single
+// particle is final at once (returns 1, a final set), else it is pushed
+template <typename T, int D>
+__device__ __forceinline__ unsigned push_set(unsigned *err, const WarpTile<T, D> &S, int b,
+                                             int m, int par) {
+  if (m == 1) {
+    mark_final<T, D>(S, b, S.idx(par)[b], kHeadSingle);
+    return 1u;
+  }
+  push_rec<T, D>(err, S, size_class(m), pack_rec(b, m, par));
+  return 0u;
 }
 
 template <typename T, int D>
 __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D> &S,
-                                           const int32_t *perm, int64_t gb, int b, int m,
-                                           int par, Counters &cnt) {
-  if (m == 1) {
-    emit_single<T, D>(P, S, perm, gb, b, S.idx(par)[b]);
-    cnt.leaves += 1;
-    return;
-  }
-  push_rec<T, D>(P, S, size_class(m), pack_rec(b, m, par));
+                                           const int32_t *, int64_t, int b, int m, int par,
+                                           Counters &cnt) {
+  cnt.leaves += push_set<T, D>(P.err, S, b, m, par);
 }
 
 // A rare event of one decision: near-tie bits (kNear*) and rechecks
@@ -180,13 +191,44 @@ __device__ __forceinline__ void note_event(const WarpTile<T, D> &S, unsigned bit
   note_event_words(S.ev, bits);
 }
 
+// Longest run of terms one lane adds in plain FP32 before the run is folded
+// into the compensated sums (bounds the error of long sums).
+constexpr int kRunBlock = 32;
+
+// moments of the set's particles i = i0, i0 + step, ... < m about s, with
+// every kRunBlock consecutive terms of a lane summed in plain FP32 and then
+// folded exactly (two-sum) into M
+template <typename T, int D>
+__device__ __forceinline__ void accumulate_blocked(Moments<T, D> &M, const WarpTile<T, D> &S,
+                                                   const uint16_t *ix, int b, int m, int i0,
+                                                   int step, const T *s) {
+  for (int blk = i0; blk < m; blk += step * kRunBlock) {
+    Moments<T, D> R;
+    R.zero();
+    const int end = min(m, blk + step * kRunBlock);
+#pragma unroll 4
+    for (int i = blk; i < end; i += step) {
+      const int j = ix[b + i];
+      T q[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+      R.add(S.col(D)[j], q, s);
+    }
+    M.merge(R);
+  }
+}
+
 // FP32 storage: Steps 2-6 for one set in FP64 from its particles, by the
 // whole warp (warp-uniform call), when an FP32 decision or cut value on it
 // was closer than its error bound.  The cut value is the FP64 centroid
 // rounded down to float; particles in the FP64 near band are cut near-ties.
+// Called from the kernel's round loop after a round (not from inside the
+// round bodies), where little else is live.  Returns the set's counts:
+// leaves (bits 0-1), splits (bit 2), degenerate cuts (bit 3), and the set's
+// size when it was split (bits 8-20, for the depth sum).
 template <typename T, int D, bool VAR>
-__device__ void exact_set(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                          int64_t gb, int b, int m, int par, int lane, Counters &cnt) {
+__device__ __forceinline__ unsigned exact_set(WarpTile<T, D> S, unsigned *err, int b, int m,
+                                           int par, int lane) {
   const unsigned full = 0xffffffffu;
   const uint16_t *ix = S.idx(par);
   // the FP64 sums go through this warp's slot of the wide-round scratch
@@ -225,7 +267,7 @@ __device__ void exact_set(const Problem &P, const WarpTile<T, D> &S, const int32
   double sd[D];
 #pragma unroll
   for (int l = 0; l < D; ++l) sd[l] = (double)s[l];
-  const Cut cut = decide_fp64<D, VAR>(P, xs[0], xs + 1, xs + 1 + D, sd, m);
+  const Cut cut = decide_fp64<D, VAR, DecideConsts>(*S.dk, xs[0], xs + 1, xs + 1 + D, sd, m);
   const int np = par ^ 1;
   int cntL = 0;
   bool nr = false;
@@ -254,46 +296,54 @@ __device__ void exact_set(const Problem &P, const WarpTile<T, D> &S, const int32
   __syncwarp();
   if (lane == 0) note_event<T, D>(S, kRechecked | cut.near | (nr ? kNearCut : 0u));
   const bool degenerate = !cut.leaf && (cntL == 0 || cntL == m);
+  unsigned counts = 0u;
   if (cut.leaf || degenerate) {
     const uint16_t *fx = S.idx(cut.leaf ? par : np);
     const int h = head_code(m);
     for (int i = lane; i < m; i += 32) mark_final<T, D>(S, b + i, fx[b + i], i == 0 ? h : 0);
-  }
-  if (lane == 0) {
-    if (cut.leaf || degenerate) {
-      cnt.leaves += 1;
-      if (degenerate) cnt.degenerate += 1;
-    } else {
-      cnt.splits += 1;
-      cnt.depth += (unsigned long long)m;
-      push_child<T, D>(P, S, perm, gb, b, cntL, np, cnt);
-      push_child<T, D>(P, S, perm, gb, b + cntL, m - cntL, np, cnt);
-    }
+    counts = 1u | (degenerate ? 8u : 0u);
+  } else if (lane == 0) {
+    const unsigned lv = push_set<T, D>(err, S, b, cntL, np) + push_set<T, D>(err, S, b + cntL,
+                                                                          m - cntL, np);
+    counts = lv | 4u | ((unsigned)m << 8);
   }
   __syncwarp();
+  return counts;
 }
 
-// the sets of this warp marked in `pend` (a bit at each set's first lane,
-// set ranges broadcast from there), one at a time in FP64 (exact_set)
+template <typename T, int D, bool VAR>
+__device__ __forceinline__ void exact_one(const Problem &P, const WarpTile<T, D> &S, int b,
+                                          int m, int par, int lane, Counters &cnt) {
+  const unsigned r = exact_set<T, D, VAR>(S, P.err, b, m, par, lane);
+  if (lane == 0) {
+    cnt.leaves += r & 3u;
+    cnt.splits += (r >> 2) & 1u;
+    cnt.degenerate += (r >> 3) & 1u;
+    cnt.depth += r >> 8;
+  }
+}
+
+// the sets of this warp marked in `pend` (a bit at a lane holding the set's
+// record `rec`), one at a time in FP64 (exact_set)
 template <typename T, int D, bool VAR>
 __device__ __forceinline__ void exact_sets(const Problem &P, const WarpTile<T, D> &S,
-                                           const int32_t *perm, int64_t gb, unsigned pend, int b,
-                                           int m, int par, int lane, Counters &cnt) {
-  const unsigned full = 0xffffffffu;
+                                           unsigned pend, uint32_t rec, int lane,
+                                           Counters &cnt) {
   while (pend) {
     const int src = __ffs(pend) - 1;
     pend &= pend - 1u;
-    const int bb = __shfl_sync(full, b, src), mm = __shfl_sync(full, m, src),
-              pp = __shfl_sync(full, par, src);
-    exact_set<T, D, VAR>(P, S, perm, gb, bb, mm, pp, lane, cnt);
+    const uint32_t r = __shfl_sync(0xffffffffu, rec, src);
+    exact_one<T, D, VAR>(P, S, rec_begin(r), rec_len(r), rec_par(r), lane, cnt);
   }
 }
 
 // one round of class c >= 1 for this warp: kw <= 32/G subsets, G lanes
-// each; rec is the record of the lane's group (read before the round)
-template <typename T, int D, bool VAR>
-__device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                            int64_t gb, int c, int lane, Counters &cnt, int kw, uint32_t rec) {
+// each; rec is the record of the lane's group (read before the round).
+// Returns the lanes whose set needs the FP64 recheck (exact_sets).
+template <typename T, int D, bool VAR, int TEAM>
+__device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                                int64_t gb, int c, int lane, Counters &cnt, int kw,
+                                uint32_t rec) {
   constexpr bool kF = sizeof(T) == 4;
   const unsigned full = 0xffffffffu;
   const int lg = c - 1, G = 1 << lg;
@@ -311,19 +361,27 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
   }
   Moments<T, D> M;
   M.zero();
+  int run = (m + G - 1) >> lg;
+  if (TEAM == kMaxTeam && kF && G == 32 && m > kRunBlock * 32) {
+    // sets above 1024 particles (large tiles only): FP32 runs of at most
+    // kRunBlock terms, each folded exactly into the compensated sums
+    accumulate_blocked<T, D>(M, S, ix, b, m, gl, G, s);
+    run = kRunBlock;
+  } else {
 #pragma unroll 4
-  for (int i = gl; i < m; i += G) {
-    const int j = ix[b + i];
-    T q[D];
+    for (int i = gl; i < m; i += G) {
+      const int j = ix[b + i];
+      T q[D];
 #pragma unroll
-    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
-    M.add(S.col(D)[j], q, s);
+      for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+      M.add(S.col(D)[j], q, s);
+    }
   }
   __syncwarp();
   M.group_allreduce(G);
   // Steps 3-5
   Cut cut = cut_none();
-  if (act) cut = Decider<T, D, VAR>::run(P, M, s, m, (m + G - 1) >> lg);
+  if (act) cut = Decider<T, D, VAR>::run(P, M, s, m, run);
   // FP32 storage: a decision too close to call is taken again in FP64
   bool redo = kF && cut.unsure;
   if (cut.near && gl == 0) note_event<T, D>(S, cut.near);
@@ -396,10 +454,7 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
     }
   }
   __syncwarp();
-  if (kF) {
-    const unsigned pend = __ballot_sync(full, redo && act && gl == 0);
-    if (pend) exact_sets<T, D, VAR>(P, S, perm, gb, pend, b, m, par, lane, cnt);
-  }
+  return kF ? __ballot_sync(full, redo && act && gl == 0) : 0u;
 }
 
 // A wide round: the (up to TEAM/2) pending sets of 193 or more particles,
@@ -412,10 +467,11 @@ __device__ void group_round(const Problem &P, const WarpTile<T, D> &S, const int
 // is the order one warp would write.  An FP32 decision or cut too close to
 // call is taken again in FP64 by the group's first warp.  Every warp of the
 // team calls this (the idle ones too): it contains CTA barriers.
+// Returns true when this warp must take its set's FP64 recheck (exact_set).
 template <typename T, int D, bool VAR, int TEAM>
-__device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                           int64_t gb, int lane, int wt, int sub, int W, bool act, uint32_t rec,
-                           Counters &cnt) {
+__device__ bool wide_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                          int64_t gb, int lane, int wt, int sub, int W, bool act, uint32_t rec,
+                          Counters &cnt) {
   constexpr bool kF = sizeof(T) == 4;
   Moments<T, D> *xm = static_cast<Moments<T, D> *>(S.wide);
   int *xc = reinterpret_cast<int *>(xm + kMaxTeam);
@@ -432,13 +488,19 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
   }
   Moments<T, D> M;
   M.zero();
+  int run = (m + 32 * W - 1) / (32 * W);
+  if (kF && run > kRunBlock) {
+    accumulate_blocked<T, D>(M, S, ix, b, m, wl * 32 + lane, 32 * W, s);
+    run = kRunBlock;
+  } else {
 #pragma unroll 4
-  for (int i = wl * 32 + lane; i < m; i += 32 * W) {
-    const int j = ix[b + i];
-    T q[D];
+    for (int i = wl * 32 + lane; i < m; i += 32 * W) {
+      const int j = ix[b + i];
+      T q[D];
 #pragma unroll
-    for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
-    M.add(S.col(D)[j], q, s);
+      for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
+      M.add(S.col(D)[j], q, s);
+    }
   }
   M.warp_allreduce();
   if (lane == 0) xm[wt] = M;
@@ -447,7 +509,7 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
   if (act) {
     Moments<T, D> Mt = xm[sub * W];
     for (int u = 1; u < W; ++u) Mt.merge(xm[sub * W + u]);
-    cut = Decider<T, D, VAR>::run(P, Mt, s, m, (m + 32 * W - 1) / (32 * W));
+    cut = Decider<T, D, VAR>::run(P, Mt, s, m, run);
   }
   bool redo = kF && cut.unsure;
   if (cut.near && wl == 0 && lane == 0) note_event<T, D>(S, cut.near);
@@ -529,15 +591,15 @@ __device__ void wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
     }
   }
   // redo is the same in every lane of the group's warps
-  if (kF && act && redo && wl == 0) exact_set<T, D, VAR>(P, S, perm, gb, b, m, par, lane, cnt);
+  return kF && act && redo && wl == 0;
 }
 
 // one round of two-particle sets for this warp: kw <= 32 of them, one per
 // lane; rec is the lane's record (read before the round).  An FP32 decision
 // or cut too close to call is taken again in FP64 (exact_set).
 template <typename T, int D, bool VAR>
-__device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                           int64_t gb, int lane, Counters &cnt, int kw, uint32_t rec) {
+__device__ unsigned pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
+                               int64_t gb, int lane, Counters &cnt, int kw, uint32_t rec) {
   constexpr bool kF = sizeof(T) == 4;
   const bool act = lane < kw;
   const int b = rec_begin(rec), par = rec_par(rec);
@@ -551,12 +613,18 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
       qb[l] = S.col(l)[jb];
     }
     const T wa = S.col(D)[ja], wb = S.col(D)[jb];
-    // the same sums as the general path takes for two particles
-    Moments<T, D> M;
-    M.zero();
-    M.add(wa, qa, qa);
-    M.add(wb, qb, qa);
-    const Cut cut = Decider<T, D, VAR>::run(P, M, qa, 2, 2);
+    Cut cut;
+    if constexpr (kF) {
+      // FP32 storage: the certified two-particle decision (cut by order)
+      cut = decide_pair<D, VAR>(P, wa, wb, qa, qb);
+    } else {
+      // the same sums as the general path takes for two particles
+      Moments<T, D> M;
+      M.zero();
+      M.add(wa, qa, qa);
+      M.add(wb, qb, qa);
+      cut = Decider<T, D, VAR>::run(P, M, qa, 2, 2);
+    }
     T ka = qa[0], kb = qb[0];
 #pragma unroll
     for (int l = 0; l < D; ++l)
@@ -564,16 +632,18 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
         ka = qa[l];
         kb = qb[l];
       }
-    const bool nr = !cut.leaf && !cut.unsure &&
+    const bool nr = !kF && !cut.leaf &&
                     (Decider<T, D, VAR>::near(ka, cut) || Decider<T, D, VAR>::near(kb, cut));
-    redo = kF && (cut.unsure || nr);
+    redo = kF && cut.unsure;
     if (!redo) {
       const unsigned ev = cut.near | (nr ? kNearCut : 0u);
       if (ev) note_event<T, D>(S, ev);
       bool merged = cut.leaf != 0;
       int first = ja, second = jb;
       if (!merged) {
-        const bool la = Decider<T, D, VAR>::left(ka, cut), lb = Decider<T, D, VAR>::left(kb, cut);
+        // FP32: the smaller value is in V1 (the exact centroid lies between)
+        const bool la = kF ? ka < kb : Decider<T, D, VAR>::left(ka, cut);
+        const bool lb = kF ? kb < ka : Decider<T, D, VAR>::left(kb, cut);
         if (la == lb) {
           merged = true;  // degenerate cut: the set stays whole
           cnt.degenerate += 1;
@@ -595,10 +665,7 @@ __device__ void pair_round(const Problem &P, const WarpTile<T, D> &S, const int3
       }
     }
   }
-  if (kF) {
-    const unsigned pend = __ballot_sync(0xffffffffu, redo);
-    if (pend) exact_sets<T, D, VAR>(P, S, perm, gb, pend, b, 2, par, lane, cnt);
-  }
+  return kF ? __ballot_sync(0xffffffffu, redo) : 0u;
 }
 
 // --------------------------------------------------------------- kernel
@@ -671,6 +738,20 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       S.wide = base + woff;
     }
     S.cap = cap;
+    {
+      const size_t doff = ((size_t)(static_cast<unsigned char *>(S.wide) - base) +
+                           kMaxTeam * (sizeof(Moments<T, D>) + sizeof(int)) + 15) &
+                          ~size_t(15);
+      DecideConsts *dk = reinterpret_cast<DecideConsts *>(base + doff);
+      if (tt == 0) {
+        dk->tol2_x = P.tol2_x;
+        dk->tol2_p = P.tol2_p;
+        for (int a = 0; a < 3; ++a) dk->L2[a] = P.L2[a];
+        dk->dx = P.dx;
+        dk->variant = P.variant;
+      }
+      S.dk = dk;
+    }
     if (tt < kClasses) {
       int o = cap / 2;  // classes 0 and 1 share [0, cap / 2)
       for (int c = 2; c < tt; ++c) o += class_capacity(c, cap);
@@ -789,7 +870,8 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           __syncthreads();
           if (tt == 0) S.top[c] = 0;
           __syncthreads();
-          wide_round<T, D, VAR, TEAM>(P, S, perm, gb, lane, wt, sub, W, act, rec, cnt);
+          if (wide_round<T, D, VAR, TEAM>(P, S, perm, gb, lane, wt, sub, W, act, rec, cnt))
+            exact_sets<T, D, VAR>(P, S, 1u, rec, lane, cnt);
           continue;
         }
         const int per = (c == 0) ? 32 : (32 >> (c - 1));
@@ -805,10 +887,14 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         if (tt == 0) S.top[c] = avail - k;
         __syncthreads();
         if (kw > 0) {
+          unsigned pend;
           if (c == 0)
-            pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, rec);
+            pend = pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, rec);
           else
-            group_round<T, D, VAR>(P, S, perm, gb, c, lane, cnt, kw, rec);
+            pend = group_round<T, D, VAR, TEAM>(P, S, perm, gb, c, lane, cnt, kw, rec);
+          // FP32 storage: the rare FP64 rechecks, by the whole warp, after
+          // its share of the round
+          if (sizeof(T) == 4 && pend) exact_sets<T, D, VAR>(P, S, pend, rec, lane, cnt);
         }
         __syncwarp();
       }
