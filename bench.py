@@ -36,8 +36,6 @@ METRIC = ("Mparticles/s merged and % of HBM roofline, FP32-mixed vs FP64 plain a
           "conservation error")
 UNIT = "Mparticles/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
-FP32_OPS_PEAK = 152 * 128 * 2.07e9  # FP32 lanes x SMs x max clock (instr/s)
-FP64_OPS_PEAK = 1.25e12 / 2.0       # nominal GB300 FP64 FMA rate (ops/s)
 
 
 def kernels_per_step(n_cells):
@@ -199,7 +197,18 @@ def to_device(p, mixed, dev):
             torch.from_numpy(np.ascontiguousarray(p.w)).to(dev, dt))
 
 
-def time_device(p, mixed, steps, warmup, dev, flush):
+def alu_peaks():
+    """Measured FMA rates (independent FMAs per second, every SM) in FP32 and
+    FP64, from the library's probe, and the SM count read from the device."""
+    from paper_1504_00636_gb300 import binding
+    f32, sms = binding.pma_probe_fma("mixed")
+    f64, _ = binding.pma_probe_fma("fp64")
+    return {"fp32_fma_per_s": f32, "fp64_fma_per_s": f64, "sms": sms,
+            "source": "pma_probe_fma: 8 independent FMA chains per thread, 8 CTAs x 256 "
+                      "threads per SM, best of 5 launches (CUDA events)"}
+
+
+def time_device(p, mixed, steps, warmup, dev, flush, flags=0):
     """K steps of one pma_merge each, inputs resident.  The step is captured
     once into a CUDA graph and replayed; each replay is bracketed by CUDA
     events on the capture stream (if capture fails, the same loop runs
@@ -208,7 +217,7 @@ def time_device(p, mixed, steps, warmup, dev, flush):
     import torch
     from paper_1504_00636_gb300 import binding
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min,
-                       "mixed" if mixed else "fp64")
+                       "mixed" if mixed else "fp64", flags)
     cells, pos, mom, w = to_device(p, mixed, dev)
     out = m.alloc_output(dev)
     stream = torch.cuda.Stream(dev)
@@ -258,6 +267,8 @@ def time_device(p, mixed, steps, warmup, dev, flush):
     m.sync()
     st = m.stats()
     m.close()
+    del cells, pos, mom, w, out
+    torch.cuda.empty_cache()
     return dict(ms=ms, stage=stage, stats=st, M=M, graph=graph_ok, eager_ms=eager_ms)
 
 
@@ -310,40 +321,96 @@ def time_e2e(p, mixed, steps, warmup):
     return dict(s=ts, h2d=h2d, d2h=d2h, M=M)
 
 
-def accuracy_report(p, dev, sample_cells=256, seed=0):
+def decisions_differing(tr, labels):
+    """Split decisions of one cell at which a result departs from the oracle's
+    recursion tree: walk the tree (V1-first preorder) and count the nodes
+    whose set the result does not treat alike (a leaf that is not one final
+    set of the result; a split with a final set of the result across it, or
+    whose halves come out in the other order, i.e. another axis or side);
+    nodes below a departure are not counted again.  labels[i] is the
+    result's output slot of the cell's i-th particle."""
+    import numpy as np
+    nodes = list(zip(tr.begin.tolist(), tr.end.tolist(), tr.depth.tolist(), tr.axis.tolist()))
+    by_begin = {}
+    for k, (b, e, d, ax) in enumerate(nodes):
+        by_begin.setdefault((b, d), k)
+    lab = labels[tr.perm]
+
+    def walk(k):
+        b, e, d, ax = nodes[k]
+        seg = lab[b:e]
+        if ax < 0:
+            whole = np.count_nonzero(labels == seg[0])
+            return 0 if (np.all(seg == seg[0]) and whole == e - b) else 1
+        c1 = by_begin.get((b, d + 1))
+        if c1 is None:
+            return 1
+        b1, e1 = nodes[c1][0], nodes[c1][1]
+        if np.intersect1d(lab[b1:e1], lab[e1:e]).size or (np.all(seg == seg[0])):
+            return 1
+        if e1 < e and lab[b1:e1].max() > lab[e1:e].min():
+            return 1  # the same halves, in the other order
+        c2 = by_begin.get((e1, d + 1))
+        return walk(c1) + (walk(c2) if c2 is not None else 1)
+
+    return walk(0) if nodes else 0
+
+
+def accuracy_report(p, dev, sample_cells=256, seed=0, flags=0, variant=0):
     """Mixed path vs the FP64 oracle on sampled cells (outside any timed
-    region): cells whose membership differs, worst coordinate error of the
-    merged particles (relative to each axis' mean |q|), worst per-cell
-    conservation error of W and W P (relative to sum w and sum w |p|).
-    The oracle runs on (a) the float32-rounded inputs the mixed path stores
-    and (b) the original FP64 inputs, separating input rounding from
-    accumulation."""
+    region).  Membership: cells differing, of which explained by a near-tie
+    flag of either side (unexplained must be 0), and the split decisions that
+    differ (walk of the oracle's recursion tree).  Coordinates: worst error
+    of the merged particles relative to each axis' mean |q|.  Per-cell
+    conservation of W and W P relative to sum w and sum w |p|, and the
+    relative kinetic-energy loss of both sides.  The oracle runs on (a) the
+    float32-rounded inputs the mixed path stores and (b) the original FP64
+    inputs, separating input rounding from the path's own arithmetic."""
     import torch
     import oracle
     from paper_1504_00636_gb300 import binding
     q = p.astype(np.float32)
-    m = binding.Merger(q.dx, q.dp, q.n_cells, q.n, q.cell_size, q.n_min, "mixed")
+    m = binding.Merger(q.dx, q.dp, q.n_cells, q.n, q.cell_size, q.n_min, "mixed",
+                       flags | binding.PMA_FLAG_ENERGY_STATS)
     cells, pos, mom, w = to_device(q, True, dev)
     M, out = m.merge(cells, pos, mom, w, q.tol_x, q.tol_p)
+    st = m.stats()
     g_cell = out.cell[:M].cpu().numpy()
     g_index = out.index[:q.n].cpu().numpy().astype(np.int64)
+    g_flags = out.cell_flags.cpu().numpy().astype(np.uint32)
     g_w = out.w[:M].cpu().numpy()
     g_c = np.concatenate([np.stack([t[:M].cpu().double().numpy() for t in out.pos]),
                           np.stack([t[:M].cpu().numpy() for t in out.mom])])
     m.close()
+    del cells, pos, mom, w, out
     rng = np.random.default_rng(seed)
     present = np.unique(q.cell)
     sample = np.sort(rng.choice(present, min(sample_cells, present.size), replace=False))
     first_g = np.searchsorted(g_cell, np.arange(q.n_cells))
-    rep = {"sample_cells": int(sample.size)}
+    rep = {"sample_cells": int(sample.size),
+           "gpu": {"fp64_rechecks": st["fp64_rechecks"], "cells_flagged": st["cells_flagged"],
+                   "near_stop": st["near_stop"], "near_argmax": st["near_argmax"],
+                   "near_cut": st["near_cut"],
+                   "energy_loss_rel": (st["energy_in"] - st["energy_out"]) / st["energy_in"]}}
+    g_near = (g_flags & binding.PMA_NEAR_ANY) != 0
     for tag, src in (("vs_oracle_on_f32_inputs", q), ("vs_oracle_on_f64_inputs", p)):
         sub = src.select_cells(sample)
-        r = oracle.merge_particles(sub, threads=os.cpu_count() or 1)
+        r = oracle.merge_particles(sub, threads=os.cpu_count() or 1, variant=variant)
         mask = np.isin(q.cell, sample)
         gi = g_index[mask] - first_g[q.cell[mask]]
         first_o = np.searchsorted(r.cell, np.arange(q.n_cells))
         oi = r.index.astype(np.int64) - first_o[sub.cell]
-        diff = np.unique(sub.cell[gi != oi])
+        cnt_g = np.bincount(g_cell, minlength=q.n_cells)[sample]
+        cnt_o = np.bincount(r.cell, minlength=q.n_cells)[sample]
+        diff = np.union1d(np.unique(sub.cell[gi != oi]), sample[cnt_g != cnt_o])
+        explained = (r.flags[diff] != 0) | g_near[diff]
+        # split decisions that differ, from the oracle's recursion tree
+        ndec = 0
+        for c in diff:
+            sel = sub.cell == c
+            tr = oracle.trace(sub.pos[:, sel], sub.mom[:, sel], sub.w[sel], sub.cell_size,
+                              sub.tol_x, sub.tol_p, variant=variant)
+            ndec += decisions_differing(tr, gi[sel])
         same = np.setdiff1d(sample, diff)
         go = np.isin(g_cell, same)
         oo = np.isin(r.cell, same)
@@ -353,8 +420,14 @@ def accuracy_report(p, dev, sample_cells=256, seed=0):
             got = g_c[:, go]
             scale = np.mean(np.abs(np.concatenate([sub.pos, sub.mom]).astype(np.float64)), axis=1)
             worst = float(np.max(np.abs(got - ref) / scale[:, None]))
-        rep[tag] = {"cells_differing": int(diff.size), "flagged_near_ties": int((r.flags != 0).sum()),
-                    "max_coord_err_rel": worst}
+        e_in, e_out = r.stats["energy_in"], r.stats["energy_out"]
+        rep[tag] = {"cells_differing": int(diff.size),
+                    "cells_differing_unexplained": int(np.count_nonzero(~explained)),
+                    "decisions_differing": int(ndec),
+                    "oracle_flagged_cells": int((r.flags[sample] != 0).sum()),
+                    "gpu_flagged_cells": int(g_near[sample].sum()),
+                    "max_coord_err_rel": worst,
+                    "oracle_energy_loss_rel": (e_in - e_out) / e_in if e_in else 0.0}
     # conservation against the stored (float32) inputs, every sampled cell
     mask_o = np.isin(g_cell, sample)
     wq = q.w.astype(np.float64)
@@ -383,33 +456,58 @@ def time_oracle(p, threads, reps):
     return ts, r
 
 
-def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name):
+def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name, alu):
     """Roofline of the dominant kernel: the per-cell partition of the small-cell
-    class (team_kernel, 4 warps per cell), from its live event timing."""
+    class (team_kernel, 4 warps per cell), from its live event timing.
+    Bytes: it reads every particle of the cells it owns once and writes the
+    4-byte final permutation and the head byte of every particle.  Ops: one
+    multiply-add per moment accumulator (1 + 2D) and one compare per particle
+    and tree level, F = depth_sum (2D + 2), against the measured FMA rate of
+    the path's arithmetic (FP32 for mixed, FP64 for plain).  The larger of
+    the two times is the bound that is reported."""
     b_in, _ = bytes_per_particle(p, mixed)
     t = stage_ms["warp_cells"] * 1e-3
     n = p.n
-    # per launch it reads every particle of the cells it owns once and writes
-    # the 4-byte final permutation and the head byte of every particle
     bytes_alg = n * (b_in - 4 + 4 + 1)
     D = p.dx + p.dp
     ops_alg = stats["depth_sum"] * (2 * D + 2)
     hbm = peaks["hbm_gbs"] * 1e9
-    alu_peak = FP32_OPS_PEAK if mixed else FP64_OPS_PEAK
+    alu_peak = alu["fp32_fma_per_s"] if mixed else alu["fp64_fma_per_s"]
     t_hbm, t_alu = bytes_alg / hbm, ops_alg / alu_peak
     traffic = ncu_traffic("team_kernel", workload_name, "mixed" if mixed else "fp64")
+    other = {"t_hbm_us": round(t_hbm * 1e6, 2), "t_alu_us": round(t_alu * 1e6, 2),
+             "bytes_alg": int(bytes_alg), "ops_alg": int(ops_alg)}
     if t_hbm >= t_alu:
         ach = bytes_alg / t / 1e9
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
                 "traffic": traffic, "kernel": "team_kernel",
-                "peak_source": peak_kind}
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind, **other}
     ach = ops_alg / t / 1e12
     return {"bound": "alu", "achieved": round(ach, 4), "peak": round(alu_peak / 1e12, 3),
             "unit": "Tops/s", "frac": round(ach / (alu_peak / 1e12), 4), "traffic": traffic,
             "kernel": "team_kernel",
-            "peak_source": "FP32 lanes x SMs x max clock" if mixed else
-            "nominal GB300 FP64 1.25 TFLOP/s / 2"}
+            "peak_source": "measured %s FMA rate (%s)" % ("FP32" if mixed else "FP64",
+                                                          alu["source"]), **other}
+
+
+def extra_line(name, p, mixed, steps, warmup, dev, flush, peaks, flags=0):
+    """One more configuration, timed like the headline (graph replays, L2
+    flushed between steps): Mparticles/s, ms per call, step HBM fraction of
+    the algorithmic bytes, M and the per-stage times."""
+    res = time_device(p, mixed, steps, warmup, dev, flush, flags)
+    t_ms = float(np.mean(res["ms"]))
+    b_in, b_out = bytes_per_particle(p, mixed)
+    step_bytes = p.n * (b_in + 4) + res["M"] * b_out
+    return {"workload": name, "precision": "mixed" if mixed else "fp64", "flags": flags,
+            "n": p.n, "cells": p.n_cells, "value": round(p.n / (t_ms * 1e-3) / 1e6, 2),
+            "unit": UNIT, "ms_per_step": round(t_ms, 4), "steps": steps,
+            "hbm_frac_step": round(step_bytes / (t_ms * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4),
+            "M": res["M"], "stage_ms": {k: round(x, 4) for k, x in res["stage"].items()},
+            "fp64_rechecks": res["stats"]["fp64_rechecks"],
+            "cells_flagged": res["stats"]["cells_flagged"],
+            "cells_per_path": {k: res["stats"][k] for k in
+                               ("cells_tiny", "cells_small", "cells_large", "big_cells")}}
 
 
 def main():
@@ -423,6 +521,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (counter beams, shuffled and "
+                         "momentum-norm two-stream, shower, 6D hot spots)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -469,6 +570,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    alu = alu_peaks()
     results = {}
     clocks = ClockSampler(local)
     barrier()
@@ -495,8 +597,10 @@ def main():
             hbm_frac_step=round(step_bytes / (t_ms / args.steps * 1e-3) / (peaks["hbm_gbs"] * 1e9), 4),
             M=res["M"], stage_ms={k: round(x, 4) for k, x in res["stage"].items()},
             roofline=roofline(q, mixed, res["stats"], res["stage"], peaks, peak_kind,
-                              res["M"], args.workload),
+                              res["M"], args.workload, alu),
             depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"],
+            fp64_rechecks=res["stats"]["fp64_rechecks"],
+            cells_flagged=res["stats"]["cells_flagged"],
             graph=res["graph"],
             eager_ms_per_step=round(float(np.mean(res["eager_ms"])), 4))
     head = lines[True] if True in lines else lines[False]
@@ -520,7 +624,8 @@ def main():
             "stage_ms": head["stage_ms"], "M": head["M"],
             "cuda_graph": head["graph"], "eager_ms_per_step": head["eager_ms_per_step"],
             "gpu_launches": kernels_per_step(p.n_cells) * args.steps * len(lines),
-            "clocks": clk}
+            "clocks": clk, "alu_peaks": alu,
+            "fp64_rechecks": head["fp64_rechecks"], "cells_flagged": head["cells_flagged"]}
     if mixed_head and False in lines:
         f = lines[False]
         line["fp64_plain"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
@@ -529,6 +634,31 @@ def main():
                               "speedup_mixed_over_fp64": round(head["value"] / f["value"], 3)}
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_extras and world == 1:
+        # the other configurations of the benchmark, each timed like the
+        # headline on its own inputs (fewer steps); not part of `value`
+        from paper_1504_00636_gb300 import binding, synth
+        ex = []
+        K = max(3, min(args.steps, 10))
+        cb = synth.counter_beams()
+        for mx in (True, False):
+            q = cb.astype(np.float32) if mx else cb
+            ex.append(extra_line("counter_beams (latency)", q, mx, K, 3, dev, flush, peaks))
+        ts = synth.two_stream()
+        sh = ts.shuffled(3).astype(np.float32)
+        ex.append(extra_line("two_stream shuffled", sh, True, K, 3, dev, flush, peaks))
+        ex.append(extra_line("two_stream momentum-norm CV", ts.astype(np.float32), True, K, 3,
+                             dev, flush, peaks, binding.PMA_FLAG_MOMENTUM_NORM))
+        del sh, ts
+        shw = synth.shower()
+        for mx in (True, False):
+            q = shw.astype(np.float32) if mx else shw
+            ex.append(extra_line("shower", q, mx, K, 3, dev, flush, peaks))
+        del shw, q
+        h6 = synth.hot_6d()
+        ex.append(extra_line("hot_6d", h6, True, K, 3, dev, flush, peaks))
+        del h6
+        line["other_configs"] = ex
     if mixed_head and not args.no_accuracy:
         line["accuracy_mixed"] = accuracy_report(p, dev)
     if not args.no_cpu:

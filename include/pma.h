@@ -85,6 +85,15 @@ extern "C" {
  * output count M is still <= n.
  */
 #define PMA_FLAG_CONSERVE_ENERGY 8u
+/*
+ * Energy accounting (Sec. 3, remark on energy: the centroid merge does not
+ * keep the energy; the paper measures the loss as delta E = |E0 - E| / E0).
+ * With this flag every call also sums the kinetic energy
+ * E = sum w (sqrt(1 + |p|^2) - 1) (p in units of m c) of its input and of
+ * its output in FP64 (pma_stats.energy_in / energy_out).  It costs an FP64
+ * square root per particle, so it is off by default.
+ */
+#define PMA_FLAG_ENERGY_STATS 16u
 
 typedef struct pma_handle pma_handle;
 
@@ -165,6 +174,8 @@ typedef struct pma_stats {
     int64_t cells_tiny;        /* cells per population path: up to 256 particles */
     int64_t cells_small;       /*   up to the small-class tile (and pass-through) */
     int64_t cells_large;       /*   up to one CTA's shared memory; big_cells above */
+    double energy_in;          /* with PMA_FLAG_ENERGY_STATS: kinetic energy in, */
+    double energy_out;         /*   and out (summation order varies: last bits) */
 } pma_stats;
 
 /*
@@ -291,6 +302,15 @@ int pma_merge_noalloc(const pma_config *cfg, int64_t n, const int32_t *cells,
                       const void *const *pos, const void *const *mom,
                       const void *weights, double tol_x, double tol_p,
                       const pma_output *out, int64_t *count_host, void *stream);
+
+/*
+ * Measured compute ceiling (no counterpart in the paper; used to place the
+ * partition kernels on a roofline): the rate of independent fused
+ * multiply-adds per second on the current device in FP32 (PMA_MIXED) or
+ * FP64 (PMA_FP64), best of five timed launches over every SM, and the SM
+ * count.  Allocates a small device buffer; synchronous.
+ */
+int pma_probe_fma(int precision, double *fma_per_s, int *sm_count);
 
 /* Release the handle and its device memory (NULL is accepted). */
 int pma_destroy(pma_handle *h);

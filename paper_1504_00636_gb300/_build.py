@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpma.so")
-SOURCES = ["api.cu", "bin.cu", "split.cu", "warp.cu", "warp_var.cu", "emit.cu"]
+SOURCES = ["api.cu", "bin.cu", "split.cu", "warp.cu", "warp_var.cu", "emit.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -30,6 +30,7 @@ PMA_FLAG_NO_INDEX = 1
 PMA_FLAG_SPLIT_NORMALIZED = 2
 PMA_FLAG_MOMENTUM_NORM = 4
 PMA_FLAG_CONSERVE_ENERGY = 8
+PMA_FLAG_ENERGY_STATS = 16
 PMA_NEAR_STOP = 1
 PMA_NEAR_ARGMAX = 2
 PMA_NEAR_CUT = 4
@@ -39,7 +40,7 @@ PMA_NEAR_ANY = PMA_NEAR_STOP | PMA_NEAR_ARGMAX | PMA_NEAR_CUT
 SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
            "pma_set_timing", "pma_get_timing", "pma_merge_noalloc", "pma_destroy",
            "pma_error_string", "pma_last_error", "pma_set_wait_limit",
-           "pma_test_withhold_status", "pma_test_status_of_bits")
+           "pma_test_withhold_status", "pma_test_status_of_bits", "pma_probe_fma")
 PMA_NOALLOC_MAX_N = 65536
 PMA_NOALLOC_MAX_CELLS = 65536
 PMA_N_STAGES = 7
@@ -65,7 +66,8 @@ class pma_stats(ctypes.Structure):
         "n_in", "n_out", "cells_merged", "cells_passthrough", "splits", "leaves",
         "depth_sum", "degenerate_cuts", "big_cells", "sorted_input", "near_stop",
         "near_argmax", "near_cut", "fp64_rechecks", "cells_flagged", "cells_tiny",
-        "cells_small", "cells_large")]
+        "cells_small", "cells_large")] + [("energy_in", ctypes.c_double),
+                                           ("energy_out", ctypes.c_double)]
 
 
 class PmaError(RuntimeError):
@@ -116,6 +118,9 @@ def load(build_if_missing: bool = True):
             lib.pma_set_wait_limit.restype = ctypes.c_int
             lib.pma_test_withhold_status.argtypes = [P, ctypes.c_int]
             lib.pma_test_withhold_status.restype = ctypes.c_int
+            lib.pma_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int)]
+            lib.pma_probe_fma.restype = ctypes.c_int
             lib.pma_test_status_of_bits.argtypes = [ctypes.c_uint]
             lib.pma_test_status_of_bits.restype = ctypes.c_int
             lib.pma_destroy.argtypes = [P]
@@ -204,6 +209,15 @@ def pma_set_wait_limit(handle, wait_ns: int) -> None:
 
 def pma_test_withhold_status(handle, tile: int) -> None:
     _check(load().pma_test_withhold_status(handle, int(tile)), handle)
+
+
+def pma_probe_fma(precision: str):
+    """Measured independent-FMA rate per second ("mixed": FP32, "fp64") and
+    the SM count of the current device."""
+    r, sms = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(load().pma_probe_fma(PMA_MIXED if precision == "mixed" else PMA_FP64,
+                                ctypes.byref(r), ctypes.byref(sms)))
+    return r.value, sms.value
 
 
 def pma_get_stats(handle) -> dict:

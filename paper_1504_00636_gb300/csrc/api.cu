@@ -45,6 +45,7 @@ struct Ctl {
   int32_t pad;
   int64_t count;
   unsigned long long stats[kStCount];
+  double energy[2];  // kinetic energy in and out (PMA_FLAG_ENERGY_STATS)
 };
 
 constexpr int kRing = 64;  // timed calls kept for pma_get_timing
@@ -91,6 +92,7 @@ struct pma_handle {
   unsigned long long *bin_status = nullptr;
   int32_t *tile_count = nullptr;
   long long *tile_prefix = nullptr;
+  double *energy_tiles = nullptr;  // [2][emit tiles] partial energy sums
   int4 *pieces = nullptr;
   Ctl *ctl = nullptr;
   Ctl *ctl_host = nullptr;
@@ -133,6 +135,7 @@ cudaError_t dalloc(T **p, size_t count) {
 void free_all(pma_handle *h) {
   void *ptrs[] = {h->counts, h->cell_begin, h->radix_count, h->radix_status, h->perm, h->perm_tmp, h->perm_final,
                   h->big_list, h->head, h->bin_status, h->tile_count, h->tile_prefix,
+                  h->energy_tiles,
                   h->pieces, h->ctl, h->warp_list, h->block_list, h->tiny_list, h->fin, h->cell_flags,
                   h->stage.cells, h->stage.w, h->stage.out_cell,
                   h->stage.out_w, h->stage.out_index};
@@ -185,6 +188,8 @@ int status_from_ctl(pma_handle *h) {
   s.cells_tiny = c.tiny_count;
   s.cells_small = c.warp_count;
   s.cells_large = c.block_count;
+  s.energy_in = c.energy[0];
+  s.energy_out = c.energy[1];
   switch (status_of_bits(c.err)) {
     case PMA_ERR_INPUT:
       return fail(h, PMA_ERR_INPUT,
@@ -243,7 +248,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
   if (cfg->precision != PMA_FP64 && cfg->precision != PMA_MIXED) return PMA_ERR_INVALID_ARG;
   if (cfg->capacity < 0 || cfg->capacity > INT32_MAX) return PMA_ERR_INVALID_ARG;
   if (cfg->flags & ~(PMA_FLAG_NO_INDEX | PMA_FLAG_SPLIT_NORMALIZED | PMA_FLAG_MOMENTUM_NORM |
-                     PMA_FLAG_CONSERVE_ENERGY))
+                     PMA_FLAG_CONSERVE_ENERGY | PMA_FLAG_ENERGY_STATS))
     return PMA_ERR_INVALID_ARG;
   for (int a = 0; a < cfg->dx; ++a)
     if (!(cfg->cell_size[a] > 0.0) || !std::isfinite(cfg->cell_size[a]))
@@ -300,6 +305,7 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
             dalloc(&h->bin_status, h->bin_tiles) == cudaSuccess &&
             dalloc(&h->tile_count, h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->tile_prefix, h->emit_tiles_max) == cudaSuccess &&
+            dalloc(&h->energy_tiles, 2 * (size_t)h->emit_tiles_max) == cudaSuccess &&
             dalloc(&h->pieces, h->max_pieces) == cudaSuccess && dalloc(&h->ctl, 1) == cudaSuccess &&
             cudaMallocHost(reinterpret_cast<void **>(&h->ctl_host), sizeof(Ctl)) == cudaSuccess;
   h->fin_stride = Npad;
@@ -512,6 +518,9 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   m.tile_count = h->tile_count;
   m.tile_prefix = h->tile_prefix;
   m.tiles = tiles;
+  m.energy = (h->cfg.flags & PMA_FLAG_ENERGY_STATS) ? h->ctl->energy : nullptr;
+  m.energy_tiles = h->energy_tiles;
+  m.energy_ticket = &h->ctl->emit_ticket;
   e = launch_emit(m, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "emit launch");
   mark(h, 6, st);

@@ -173,6 +173,12 @@ size_t emit_smem_bytes(int D, int mixed) {
   return (size_t)(D + 1) * kEmitTile * (mixed ? 4 : 8) + (size_t)kEmitTile * 4;
 }
 
+// kinetic energy w (sqrt(1 + p^2) - 1) of weight w and momentum squared p2
+// (in m c units), in the form without cancellation for small p2
+__device__ __forceinline__ double kinetic(double w, double p2) {
+  return w * p2 / (sqrt(1.0 + p2) + 1.0);
+}
+
 // EC: one final set of m >= 2 members at positions [p, e) of the staged
 // arrays (in this tile's shared memory below t0 + cnt, else in global
 // memory), first output slot `slot`.  m = 2: both members as they are.
@@ -184,7 +190,8 @@ size_t emit_smem_bytes(int D, int mixed) {
 // slot (a pair: each to its own, the lower input index first).
 template <typename T>
 __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_perm,
-                           int64_t t0, int cnt, int64_t p, int64_t e, long long slot) {
+                           int64_t t0, int cnt, int64_t p, int64_t e, long long slot,
+                           double &ein, double &eout) {
   const int D = a.dx + a.dp;
   auto raw = [&](int l, int64_t r) -> T {
     return r < t0 + cnt ? s_col[l * kEmitTile + (int)(r - t0)]
@@ -198,8 +205,18 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
       const int o = orig(r);
       if (a.out_index && (unsigned)o < (unsigned)a.n) a.out_index[o] = (int32_t)(slot + t);
       for (int l = 0; l < a.dx; ++l) static_cast<T *>(a.out_pos[l])[slot + t] = raw(l, r);
-      for (int l = 0; l < a.dp; ++l) a.out_mom[l][slot + t] = to_f64<T>(raw(a.dx + l, r));
-      a.out_w[slot + t] = to_f64<T>(raw(D, r));
+      double p2 = 0.0;
+      for (int l = 0; l < a.dp; ++l) {
+        const double q = to_f64<T>(raw(a.dx + l, r));
+        a.out_mom[l][slot + t] = q;
+        p2 = fma(q, q, p2);
+      }
+      const double w = to_f64<T>(raw(D, r));
+      a.out_w[slot + t] = w;
+      if (a.energy) {
+        ein += kinetic(w, p2);
+        eout += kinetic(w, p2);
+      }
     }
     return;
   }
@@ -219,6 +236,7 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
       }
     }
     E = fma(w, sqrt(1.0 + p2), E);
+    if (a.energy) ein += kinetic(w, p2);
     const int o = orig(r);
     if (a.out_index && (unsigned)o < (unsigned)a.n) a.out_index[o] = (int32_t)slot;
   }
@@ -293,11 +311,17 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
   for (int t = 0; t < 2; ++t) {
     const long long s = slot + t;
     a.out_w[s] = Wh;
+    double p2 = 0.0;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       if (l < a.dx) static_cast<T *>(a.out_pos[l])[s] = (T)(SX[l] * inv);
-      if (l < a.dp) a.out_mom[l][s] = t == 0 ? Pm[l] + da[l] : Pm[l] - da[l];
+      if (l < a.dp) {
+        const double q = t == 0 ? Pm[l] + da[l] : Pm[l] - da[l];
+        a.out_mom[l][s] = q;
+        p2 = fma(q, q, p2);
+      }
     }
+    if (a.energy) eout += kinetic(Wh, p2);
   }
 }
 
@@ -354,6 +378,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     return;
   }
   bool bad = false, internal = false;
+  double ein = 0.0, eout = 0.0;  // kinetic energy in and out (a.energy only)
+  int2 mg[kEmitChunk];           // this thread's merged heads: (offset, slot)
+  unsigned mmask = 0u;
 #pragma unroll
   for (int j = 0; j < kEmitChunk; ++j) {
     const int off = j * kEmitThreads + tid;
@@ -390,22 +417,40 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
           static_cast<T *>(a.out_pos[l])[slot] = v;
         }
       }
+      double p2 = 0.0;
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
         if (l < a.dp) {
           const T v = s_col[(a.dx + l) * kEmitTile + off];
           bad |= !isfinite(v);
-          a.out_mom[l][slot] = to_f64<T>(v);
+          const double q = to_f64<T>(v);
+          a.out_mom[l][slot] = q;
+          if (a.energy) p2 = fma(q, q, p2);
         }
       }
       const T w = s_col[D * kEmitTile + off];
       bad |= !(w > T(0)) || !isfinite(w);
       a.out_w[slot] = to_f64<T>(w);
+      if (a.energy) {
+        const double k = kinetic(to_f64<T>(w), p2);
+        ein += k;
+        eout += k;
+      }
     } else {
       // merged set: summed below, densely, by the whole CTA
-      const int k = atomicAdd(&s_nmerged, 1);
-      s_merged[k] = make_int2(off, (int)slot);
+      mg[j] = make_int2(off, (int)slot);
+      mmask |= 1u << j;
     }
+  }
+  {
+    // the merged heads in position order (a scan, not an atomic), so that
+    // each set is summed by the same thread on every run
+    int total;
+    int at = block_exclusive_scan(__popc(mmask), s_warp, &total);
+#pragma unroll
+    for (int j = 0; j < kEmitChunk; ++j)
+      if (mmask & (1u << j)) s_merged[at++] = mg[j];
+    if (tid == 0) s_nmerged = total;
   }
   __syncthreads();
   for (int k = tid; k < s_nmerged; k += kEmitThreads) {
@@ -425,7 +470,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       e = a.n;
     }
     if (EC) {
-      energy_set<T>(a, s_col, s_perm, t0, cnt, t0 + off, e, slot_m);
+      energy_set<T>(a, s_col, s_perm, t0, cnt, t0 + off, e, slot_m, ein, eout);
       continue;
     }
     double W = 0.0, S1[kMaxD];
@@ -436,30 +481,81 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       for (int r = off; r < (int)(e - t0); ++r) {
         const double w = to_f64<T>(s_col[D * kEmitTile + r]);
         W += w;
+        double p2 = 0.0;
 #pragma unroll
         for (int l = 0; l < kMaxD; ++l)
-          if (l < D) S1[l] = fma(w, to_f64<T>(s_col[l * kEmitTile + r]), S1[l]);
+          if (l < D) {
+            const double q = to_f64<T>(s_col[l * kEmitTile + r]);
+            S1[l] = fma(w, q, S1[l]);
+            if (l >= a.dx) p2 = fma(q, q, p2);
+          }
+        if (a.energy) ein += kinetic(w, p2);
       }
     } else {
       for (int64_t r = t0 + off; r < e; ++r) {
         const double w = to_f64<T>(static_cast<const T *>(a.fin[D])[r]);
         W += w;
+        double p2 = 0.0;
 #pragma unroll
         for (int l = 0; l < kMaxD; ++l)
-          if (l < D) S1[l] = fma(w, to_f64<T>(static_cast<const T *>(a.fin[l])[r]), S1[l]);
+          if (l < D) {
+            const double q = to_f64<T>(static_cast<const T *>(a.fin[l])[r]);
+            S1[l] = fma(w, q, S1[l]);
+            if (l >= a.dx) p2 = fma(q, q, p2);
+          }
+        if (a.energy) ein += kinetic(w, p2);
       }
     }
     const double inv = 1.0 / W;
     a.out_w[slot_m] = W;
+    double P2 = 0.0;
 #pragma unroll
     for (int l = 0; l < kMaxD; ++l) {
       if (l < D) {
         const double v = S1[l] * inv;
-        if (l < 3 && l < a.dx)
+        if (l < 3 && l < a.dx) {
           static_cast<T *>(a.out_pos[l])[slot_m] = (T)v;
-        else
+        } else {
           a.out_mom[l - a.dx][slot_m] = v;
+          P2 = fma(v, v, P2);
+        }
       }
+    }
+    if (a.energy) eout += kinetic(W, P2);
+  }
+  if (a.energy) {
+    // kinetic energy in and out: block sums per tile, then the last CTA to
+    // finish adds the tiles up in tile order (the same sum on every run)
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      ein += __shfl_xor_sync(0xffffffffu, ein, o);
+      eout += __shfl_xor_sync(0xffffffffu, eout, o);
+    }
+    __shared__ double s_e[2][kEmitThreads / 32];
+    __shared__ int s_last;
+    if ((tid & 31) == 0) {
+      s_e[0][tid >> 5] = ein;
+      s_e[1][tid >> 5] = eout;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double x = 0.0, y = 0.0;
+      for (int w = 0; w < kEmitThreads / 32; ++w) {
+        x += s_e[0][w];
+        y += s_e[1][w];
+      }
+      a.energy_tiles[blockIdx.x] = x;
+      a.energy_tiles[a.tiles + blockIdx.x] = y;
+      __threadfence();
+      s_last = atomicAdd(a.energy_ticket, 1) == a.tiles - 1;
+    }
+    __syncthreads();
+    if (s_last && tid < 2) {
+      __threadfence();
+      const volatile double *t = a.energy_tiles + (size_t)tid * a.tiles;
+      double v = 0.0;
+      for (int k = 0; k < a.tiles; ++k) v += t[k];
+      a.energy[tid] = v;
     }
   }
   if (bad) atomicOr(a.err, kErrInput);

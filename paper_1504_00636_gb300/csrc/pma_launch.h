@@ -86,6 +86,9 @@ struct EmitArgs {
   int32_t *tile_count;    // [tiles] heads per tile
   long long *tile_prefix; // [tiles] heads before each tile
   int32_t tiles;
+  double *energy;         // [2] kinetic energy in and out, or null
+  double *energy_tiles;   // [2][tiles] per-tile partial sums (workspace)
+  int32_t *energy_ticket; // CTAs done (zeroed by the caller); the last one sums
 };
 int emit_tiles_for(int64_t n);
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st);

@@ -28,13 +28,9 @@ from . import binding, synth
 
 
 def energy(w, mom):
-    """Kinetic energy sum w (sqrt(1 + |p|^2) - 1); numpy or torch arrays,
-    mom of shape [dp, M].  Computed as w |p|^2 / (sqrt(1 + |p|^2) + 1), which
-    has no cancellation for small |p|."""
-    if type(w).__module__.startswith("torch"):
-        import torch
-        p2 = (mom.double() ** 2).sum(0)
-        return float((w.double() * p2 / (torch.sqrt(1.0 + p2) + 1.0)).sum())
+    """Kinetic energy sum w (sqrt(1 + |p|^2) - 1) of host arrays (mom of
+    shape [dp, M]), for checks on the host.  Computed as
+    w |p|^2 / (sqrt(1 + |p|^2) + 1), which has no cancellation for small |p|."""
     p2 = np.sum(np.asarray(mom, dtype=np.float64) ** 2, axis=0)
     return float(np.sum(np.asarray(w, dtype=np.float64) * p2 / (np.sqrt(1.0 + p2) + 1.0)))
 
@@ -42,18 +38,19 @@ def energy(w, mom):
 def tolerance_scan(p, tol_x, tol_p, precision="mixed", flags=0, device="cuda"):
     """Merge the particles ``p`` (a ``synth.Particles``) for every (T_X, T_P)
     pair; returns a list of dicts with tol_x, tol_p, M, ratio = M/N,
-    dE = (E_in - E_out) / E_in and the call time in ms."""
+    dE = (E_in - E_out) / E_in (the library's FP64 energy accounting,
+    PMA_FLAG_ENERGY_STATS) and the call time in ms."""
     import torch
     dev = torch.device(device)
     q = p.astype(np.float32) if precision == "mixed" else p
     dt = torch.float32 if precision == "mixed" else torch.float64
-    m = binding.Merger(q.dx, q.dp, q.n_cells, q.n, q.cell_size, q.n_min, precision, flags)
+    m = binding.Merger(q.dx, q.dp, q.n_cells, q.n, q.cell_size, q.n_min, precision,
+                       flags | binding.PMA_FLAG_ENERGY_STATS)
     try:
         cells = torch.from_numpy(q.cell).to(dev)
         pos = [torch.from_numpy(np.ascontiguousarray(q.pos[a])).to(dev, dt) for a in range(q.dx)]
         mom = [torch.from_numpy(np.ascontiguousarray(q.mom[a])).to(dev, dt) for a in range(q.dp)]
         w = torch.from_numpy(np.ascontiguousarray(q.w)).to(dev, dt)
-        e_in = energy(w, torch.stack(mom))
         out = m.alloc_output(dev, index=False)
         rows = []
         for tx in tol_x:
@@ -62,7 +59,8 @@ def tolerance_scan(p, tol_x, tol_p, precision="mixed", flags=0, device="cuda"):
                 t0 = time.perf_counter()
                 M, out = m.merge(cells, pos, mom, w, float(tx), float(tp), out=out)
                 t1 = time.perf_counter()
-                e_out = energy(out.w[:M], torch.stack([c[:M] for c in out.mom]))
+                st = m.stats()
+                e_in, e_out = st["energy_in"], st["energy_out"]
                 rows.append(dict(tol_x=float(tx), tol_p=float(tp), M=int(M),
                                  ratio=M / max(q.n, 1), dE=(e_in - e_out) / e_in,
                                  ms=1e3 * (t1 - t0)))

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1504_00636_gb300 import binding, synth
+from paper_1504_00636_gb300 import binding, scan, synth
 
 from parity import compare, conservation, run_gpu
 
@@ -58,3 +58,29 @@ def test_energy_mode_keeps_the_partition():
     assert ec["stats"]["leaves"] == lit["stats"]["leaves"]
     sizes = np.bincount(lit["index"], minlength=lit["count"])
     assert ec["count"] == int(np.sum(np.where(sizes >= 2, 2, 1)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_energy_stats_match_the_oracle_and_the_outputs(precision):
+    # PMA_FLAG_ENERGY_STATS: FP64 kinetic energy of the input and of the
+    # output (the paper's delta E, Sec. 3 remark on energy), summed in a
+    # fixed order (identical on every call)
+    p = synth.shower(grid=(24, 24))
+    if precision == "mixed":
+        p = p.astype(np.float32)
+    flags = binding.PMA_FLAG_ENERGY_STATS
+    g = run_gpu(p, precision, flags=flags)
+    st = g["stats"]
+    r = oracle.merge_particles(p, threads=8)
+    assert st["energy_in"] == pytest.approx(r.stats["energy_in"], rel=1e-12)
+    assert st["energy_in"] == pytest.approx(scan.energy(p.w, p.mom), rel=1e-12)
+    assert st["energy_out"] == pytest.approx(scan.energy(g["w"], g["mom"]), rel=1e-12)
+    if not (r.flags.any() or (g["flags"] & binding.PMA_NEAR_ANY).any()):
+        assert st["energy_out"] == pytest.approx(r.stats["energy_out"], rel=1e-12)
+    assert st["energy_out"] <= st["energy_in"] * (1 + 1e-12)  # centroids lose energy
+    g2 = run_gpu(p, precision, flags=flags)
+    assert g2["stats"]["energy_in"] == st["energy_in"]
+    assert g2["stats"]["energy_out"] == st["energy_out"]
+    # with the energy-conserving replacement, out equals in
+    ge = run_gpu(p, precision, flags=flags | EC)
+    assert ge["stats"]["energy_out"] == pytest.approx(ge["stats"]["energy_in"], rel=1e-12)

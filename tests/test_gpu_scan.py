@@ -17,7 +17,7 @@ def test_scan_identities_and_monotonicity():
     for tp in tps:
         # in-cell positions have Delta_x <= 1/2: T_X = 0.5 and 1.0 coincide
         assert by[(0.5, tp)]["M"] == by[(1.0, tp)]["M"]
-        assert by[(0.5, tp)]["dE"] == by[(1.0, tp)]["dE"]
+        assert by[(0.5, tp)]["dE"] == by[(1.0, tp)]["dE"]  # same partition, same sums
     for tx in (0.25, 0.5, 1.0):
         Ms = [by[(tx, tp)]["M"] for tp in tps]
         dEs = [by[(tx, tp)]["dE"] for tp in tps]

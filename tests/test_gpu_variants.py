@@ -56,4 +56,4 @@ def test_variants_differ_from_the_literal_rule_on_gpu():
 
 def test_unknown_flags_are_rejected():
     with pytest.raises(binding.PmaError):
-        binding.Merger(1, 3, 4, 16, flags=16)
+        binding.Merger(1, 3, 4, 16, flags=32)
