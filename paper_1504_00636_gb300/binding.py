@@ -40,7 +40,9 @@ PMA_NEAR_ANY = PMA_NEAR_STOP | PMA_NEAR_ARGMAX | PMA_NEAR_CUT
 SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_stats",
            "pma_set_timing", "pma_get_timing", "pma_merge_noalloc", "pma_destroy",
            "pma_error_string", "pma_last_error", "pma_set_wait_limit",
-           "pma_test_withhold_status", "pma_test_status_of_bits", "pma_probe_fma")
+           "pma_test_withhold_status", "pma_test_status_of_bits", "pma_probe_fma",
+           "pma_get_classes", "pma_set_classes", "pma_tune", "pma_tune_cache_lookup",
+           "pma_tune_cache_store")
 PMA_NOALLOC_MAX_N = 65536
 PMA_NOALLOC_MAX_CELLS = 65536
 PMA_N_STAGES = 7
@@ -118,6 +120,19 @@ def load(build_if_missing: bool = True):
             lib.pma_set_wait_limit.restype = ctypes.c_int
             lib.pma_test_withhold_status.argtypes = [P, ctypes.c_int]
             lib.pma_test_withhold_status.restype = ctypes.c_int
+            caps = ctypes.POINTER(ctypes.c_int32)
+            lib.pma_get_classes.argtypes = [P, caps]
+            lib.pma_get_classes.restype = ctypes.c_int
+            lib.pma_set_classes.argtypes = [P, caps]
+            lib.pma_set_classes.restype = ctypes.c_int
+            lib.pma_tune.argtypes = [P, ctypes.c_int64, P, P, P, P, ctypes.c_double,
+                                     ctypes.c_double, ctypes.POINTER(pma_output), P]
+            lib.pma_tune.restype = ctypes.c_int
+            lib.pma_tune_cache_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, caps]
+            lib.pma_tune_cache_lookup.restype = ctypes.c_int
+            lib.pma_tune_cache_store.argtypes = [ctypes.c_char_p, ctypes.c_char_p, caps,
+                                                 ctypes.c_double]
+            lib.pma_tune_cache_store.restype = ctypes.c_int
             lib.pma_probe_fma.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int)]
             lib.pma_probe_fma.restype = ctypes.c_int
@@ -218,6 +233,37 @@ def pma_probe_fma(precision: str):
     _check(load().pma_probe_fma(PMA_MIXED if precision == "mixed" else PMA_FP64,
                                 ctypes.byref(r), ctypes.byref(sms)))
     return r.value, sms.value
+
+
+def pma_get_classes(handle):
+    """(cap_t, cap_w, cap): the population limits of the one-warp, 4-warp and
+    8-warp team paths."""
+    c = (ctypes.c_int32 * 3)()
+    _check(load().pma_get_classes(handle, c), handle)
+    return tuple(c)
+
+
+def pma_set_classes(handle, caps) -> None:
+    c = (ctypes.c_int32 * 3)(*caps)
+    _check(load().pma_set_classes(handle, c), handle)
+
+
+def pma_tune(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_output, stream=0):
+    """Raw call (device pointers as ints): time the candidate classes on the
+    input and keep the fastest (see include/pma.h)."""
+    _check(load().pma_tune(handle, n, cells, _ptrs(pos), _ptrs(mom), weights, tol_x, tol_p,
+                           ctypes.byref(out), stream), handle)
+
+
+def pma_tune_cache_lookup(path: str, key: str):
+    c = (ctypes.c_int32 * 3)()
+    rc = load().pma_tune_cache_lookup(path.encode(), key.encode(), c)
+    return tuple(c) if rc == PMA_OK else None
+
+
+def pma_tune_cache_store(path: str, key: str, caps, ms: float) -> None:
+    c = (ctypes.c_int32 * 3)(*caps)
+    _check(load().pma_tune_cache_store(path.encode(), key.encode(), c, float(ms)))
 
 
 def pma_get_stats(handle) -> dict:
@@ -324,6 +370,23 @@ class Merger:
 
     def stats(self) -> dict:
         return pma_get_stats(self.handle)
+
+    def tune(self, cells, pos, mom, w, tol_x, tol_p, out: Output = None, stream=None):
+        """Time the population classes on these particles and keep the fastest."""
+        if out is None:
+            out = self.alloc_output(cells.device)
+        if stream is None:
+            stream = self.torch.cuda.current_stream(cells.device)
+        pma_tune(self.handle, int(cells.shape[0]), cells.data_ptr(), [p.data_ptr() for p in pos],
+                 [p.data_ptr() for p in mom], w.data_ptr(), float(tol_x), float(tol_p),
+                 out.struct(), stream=stream.cuda_stream)
+        return pma_get_classes(self.handle)
+
+    def classes(self):
+        return pma_get_classes(self.handle)
+
+    def set_classes(self, caps) -> None:
+        pma_set_classes(self.handle, caps)
 
     def set_timing(self, enable: bool = True) -> None:
         pma_set_timing(self.handle, enable)

@@ -15,9 +15,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lookback.cuh"
 #include "pma.h"
@@ -68,6 +70,7 @@ struct pma_handle {
   pma_config cfg;
   int device = 0;
   int sms = 0;
+  int smem_optin = 0;
   int D = 0;
   int mixed = 0;
   int cap = 0;
@@ -220,6 +223,99 @@ __global__ void zero_kernel(ZeroArgs z) {
     for (int64_t i = t; i < z.words[r]; i += stride) z.p[r][i] = 0u;
 }
 
+// ------------------------------------------------------ population classes
+//
+// Cells of at most cap_t particles go to one-warp teams (a small tile, many
+// cells in flight per SM, no warp waits for another), cells of at most
+// cap_w to 4-warp teams (several CTAs per SM), cells of at most cap to
+// 8-warp teams with a large tile; larger cells are cut in global memory
+// first and their pieces join the 8-warp class.
+
+struct Classes {
+  int cap_t, cap_w, cap;
+};
+
+// largest tile of at most `hi` particles whose team fits the CTA's shared memory
+int largest_tile(const pma_handle *h, int hi, int lo) {
+  int c = hi;
+  while (c > lo && team_smem(h->mixed, h->D, c) > (size_t)h->smem_optin) c -= 64;
+  return c;
+}
+
+Classes default_classes(const pma_handle *h) {
+  Classes c;
+  c.cap_w = largest_tile(h, 1024, 128);
+  c.cap_t = 256;
+  c.cap = largest_tile(h, 8191, c.cap_w);
+  return c;
+}
+
+bool classes_valid(const pma_handle *h, const Classes &c) {
+  return c.cap_t >= 2 && c.cap_t <= 1024 && c.cap_t <= c.cap_w && c.cap_w <= 1024 &&
+         c.cap_w <= c.cap && c.cap <= 8191 &&
+         team_smem(h->mixed, h->D, c.cap) <= (size_t)h->smem_optin &&
+         team_smem(h->mixed, h->D, c.cap_w) <= (size_t)h->smem_optin;
+}
+
+// set the classes and the grids of the team launches (CTAs resident per SM,
+// from the shared memory of one tile)
+void apply_classes(pma_handle *h, const Classes &c) {
+  const size_t smem_sm = (size_t)h->smem_optin + 1024;
+  h->cap_t = c.cap_t;
+  h->cap_w = c.cap_w;
+  h->cap = c.cap;
+  h->warp_grid =
+      h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap_w) + 1024)));
+  // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
+  h->tiny_grid = h->sms * std::min<int>(24, std::max<int>(1, (int)(smem_sm / (team_smem(
+                                                                     h->mixed, h->D, c.cap_t) +
+                                                                 1024))));
+  h->unit_grid =
+      h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap) + 1024)));
+}
+
+// the candidates the tuner times: tiny-class limit x small-class tile x
+// large tile (the largest that fits, or smaller so that more CTAs fit and
+// more cells are first cut in global memory)
+std::vector<Classes> class_candidates(const pma_handle *h) {
+  std::vector<Classes> v;
+  const int wmax = largest_tile(h, 1024, 128);
+  const int cmax = largest_tile(h, 8191, wmax);
+  const int ts[] = {128, 256, 512};
+  const int ws[] = {512, wmax};
+  const int cs[] = {cmax, 4096, 2048};
+  for (int t : ts)
+    for (int w : ws)
+      for (int c : cs) {
+        Classes k{std::min(t, w), w, std::min(c, cmax)};
+        if (!classes_valid(h, k)) continue;
+        bool dup = false;
+        for (const Classes &o : v) dup |= o.cap_t == k.cap_t && o.cap_w == k.cap_w && o.cap == k.cap;
+        if (!dup) v.push_back(k);
+      }
+  return v;
+}
+
+// population histogram of the cells (fractions of the particles in cells of
+// 1-64, 65-256, 257-1024, 1025-4096, 4097-8191 and more particles, in
+// twentieths): the part of the tuning key that describes the input
+std::string histogram_signature(const std::vector<int32_t> &counts) {
+  const int64_t edges[6] = {64, 256, 1024, 4096, 8191, INT64_MAX};
+  double f[6] = {0, 0, 0, 0, 0, 0}, tot = 0;
+  for (int32_t c : counts) {
+    if (c <= 0) continue;
+    int b = 0;
+    while (c > edges[b]) ++b;
+    f[b] += c;
+    tot += c;
+  }
+  char buf[96];
+  int k[6];
+  for (int b = 0; b < 6; ++b) k[b] = tot > 0 ? (int)std::lround(20.0 * f[b] / tot) : 0;
+  snprintf(buf, sizeof buf, "h=%d,%d,%d,%d,%d,%d", k[0], k[1], k[2], k[3], k[4], k[5]);
+  return buf;
+}
+
 }  // namespace
 
 extern "C" {
@@ -268,25 +364,9 @@ int pma_create(const pma_config *cfg, pma_handle **out) {
     delete h;
     return PMA_ERR_CUDA;
   }
-  // population classes: cells of up to cap_w particles go to a team of 4
-  // warps (several per SM); cells of up to cap to a team of 8 warps with the
-  // largest tile that fits one CTA; larger cells are cut in global memory
-  // first and their pieces join the large class.
-  const size_t smem_sm = (size_t)smem_optin + 1024;
-  h->cap_w = 1024;
-  while (h->cap_w > 128 && team_smem(h->mixed, h->D, h->cap_w) > (size_t)smem_optin)
-    h->cap_w -= 64;
-  h->warp_grid = h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, h->cap_w) + 1024)));
-  // tiny cells (up to 256 particles) go to one-warp teams with a small tile:
-  // many cells in flight per SM, and no warp of a team waits for another
-  h->cap_t = 256;
-  // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
-  h->tiny_grid =
-      h->sms * std::min<int>(24, std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, h->cap_t) + 1024))));
-  int cap = 8191;
-  while (cap > h->cap_w && team_smem(h->mixed, h->D, cap) > (size_t)smem_optin) cap -= 64;
-  h->cap = cap;
-  h->unit_grid = h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, cap) + 1024)));
+  h->smem_optin = smem_optin;
+  // population classes (default, or as pma_tune / pma_set_classes choose)
+  apply_classes(h, default_classes(h));
   const int64_t N = std::max<int64_t>(cfg->capacity, 1);
   const int64_t C = cfg->n_cells;
   h->bin_tiles = scan_tiles_for(C);
@@ -610,6 +690,165 @@ int pma_test_withhold_status(pma_handle *h, int tile) {
 int pma_get_stats(const pma_handle *h, pma_stats *out) {
   if (!h || !out) return PMA_ERR_INVALID_ARG;
   *out = h->stats;
+  return PMA_OK;
+}
+
+// ---------------------------------------------------------------- tuning
+
+int pma_get_classes(const pma_handle *h, int32_t caps[3]) {
+  if (!h || !caps) return PMA_ERR_INVALID_ARG;
+  caps[0] = h->cap_t;
+  caps[1] = h->cap_w;
+  caps[2] = h->cap;
+  return PMA_OK;
+}
+
+int pma_set_classes(pma_handle *h, const int32_t caps[3]) {
+  if (!h || !caps) return PMA_ERR_INVALID_ARG;
+  const Classes c{caps[0], caps[1], caps[2]};
+  if (!classes_valid(h, c)) return fail(h, PMA_ERR_INVALID_ARG, "invalid population classes");
+  if (h->pending) {
+    const int rc = pma_sync(h);
+    if (rc != PMA_OK) return rc;
+  }
+  apply_classes(h, c);
+  return PMA_OK;
+}
+
+namespace {
+
+struct CacheEntry {
+  std::string key;
+  int caps[3];
+  double ms;
+};
+
+// the cache file: a JSON object, one entry per line,
+//   "key": [cap_t, cap_w, cap, ms],
+std::vector<CacheEntry> read_cache(const char *path) {
+  std::vector<CacheEntry> v;
+  FILE *f = fopen(path, "r");
+  if (!f) return v;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    const char *a = strchr(line, '"');
+    if (!a) continue;
+    const char *b = strchr(a + 1, '"');
+    if (!b) continue;
+    const char *br = strchr(b + 1, '[');
+    if (!br) continue;
+    CacheEntry e;
+    e.key.assign(a + 1, b);
+    if (sscanf(br + 1, "%d , %d , %d , %lf", &e.caps[0], &e.caps[1], &e.caps[2], &e.ms) == 4)
+      v.push_back(e);
+  }
+  fclose(f);
+  return v;
+}
+
+bool write_cache(const char *path, const std::vector<CacheEntry> &v) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  fprintf(f, "{\n");
+  for (size_t i = 0; i < v.size(); ++i)
+    fprintf(f, "  \"%s\": [%d, %d, %d, %.6g]%s\n", v[i].key.c_str(), v[i].caps[0],
+            v[i].caps[1], v[i].caps[2], v[i].ms, i + 1 < v.size() ? "," : "");
+  fprintf(f, "}\n");
+  const bool ok = fclose(f) == 0;
+  return ok && rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+
+int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[3]) {
+  if (!path || !key || !caps) return PMA_ERR_INVALID_ARG;
+  for (const CacheEntry &e : read_cache(path))
+    if (e.key == key) {
+      for (int i = 0; i < 3; ++i) caps[i] = e.caps[i];
+      return PMA_OK;
+    }
+  return PMA_ERR_INVALID_ARG;
+}
+
+int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[3], double ms) {
+  if (!path || !key || !caps || strchr(key, '"') || strchr(key, '\n')) return PMA_ERR_INVALID_ARG;
+  std::vector<CacheEntry> v = read_cache(path);
+  bool found = false;
+  for (CacheEntry &e : v)
+    if (e.key == key) {
+      for (int i = 0; i < 3; ++i) e.caps[i] = caps[i];
+      e.ms = ms;
+      found = true;
+    }
+  if (!found) {
+    CacheEntry e;
+    e.key = key;
+    for (int i = 0; i < 3; ++i) e.caps[i] = caps[i];
+    e.ms = ms;
+    v.push_back(e);
+  }
+  return write_cache(path, v) ? PMA_OK : PMA_ERR_INVALID_ARG;
+}
+
+int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
+             const void *const *mom, const void *weights, double tol_x, double tol_p,
+             const pma_output *out, void *stream) {
+  int rc = check_common(h, n, cells, pos, mom, weights, tol_x, tol_p, out);
+  if (rc != PMA_OK) return rc;
+  if (n == 0) return PMA_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // a prefix of the input (at most 2^23 particles) stands for the whole
+  const int64_t ns = std::min<int64_t>(n, (int64_t)1 << 23);
+  pma_output o = *out;
+  o.cell_flags = nullptr;
+  int64_t M = 0;
+  rc = pma_merge(h, ns, cells, pos, mom, weights, tol_x, tol_p, &o, &M, stream);
+  if (rc != PMA_OK) return rc;
+  std::vector<int32_t> counts((size_t)h->cfg.n_cells);
+  PMA_CUDA(h, cudaMemcpy(counts.data(), h->counts, counts.size() * sizeof(int32_t),
+                         cudaMemcpyDeviceToHost));
+  char key[256];
+  snprintf(key, sizeof key, "D=%d %s flags=%u sms=%d %s", h->D, h->mixed ? "mixed" : "fp64",
+           h->cfg.flags, h->sms, histogram_signature(counts).c_str());
+  const char *cache = getenv("PMA_TUNE_CACHE");
+  int32_t caps[3];
+  if (cache && *cache && pma_tune_cache_lookup(cache, key, caps) == PMA_OK &&
+      pma_set_classes(h, caps) == PMA_OK)
+    return PMA_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PMA_CUDA(h, cudaEventCreate(&e0));
+  PMA_CUDA(h, cudaEventCreate(&e1));
+  Classes best = default_classes(h);
+  double best_ms = 1e300;
+  for (const Classes &c : class_candidates(h)) {
+    apply_classes(h, c);
+    float t[3];
+    for (int r = -1; r < 3 && rc == PMA_OK; ++r) {
+      if (r >= 0) cudaEventRecord(e0, st);
+      rc = pma_merge(h, ns, cells, pos, mom, weights, tol_x, tol_p, &o, nullptr, stream);
+      if (rc != PMA_OK) break;
+      if (r >= 0) cudaEventRecord(e1, st);
+      rc = pma_sync(h);
+      if (r >= 0 && rc == PMA_OK) cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    if (rc != PMA_OK) break;
+    std::sort(t, t + 3);
+    if (t[1] < best_ms) {
+      best_ms = t[1];
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  apply_classes(h, best);
+  if (rc != PMA_OK) return rc;
+  if (cache && *cache) {
+    caps[0] = best.cap_t;
+    caps[1] = best.cap_w;
+    caps[2] = best.cap;
+    pma_tune_cache_store(cache, key, caps, best_ms);
+  }
   return PMA_OK;
 }
 
