@@ -5,8 +5,10 @@
 // synchronisation:
 //   hist / scan             Step 1: per-cell counts and first positions
 //   radix prep / passes     Step 1 for ungrouped input: stable sort by cell
-//   big_kernel              cells too large for shared memory: top cuts in
-//                           global memory until every piece fits
+//   cluster_kernel          cells too large for shared memory: top cuts in
+//                           global memory by a 4-CTA cluster per cell
+//                           (partial sums through distributed shared
+//                           memory) until every piece fits
 //   team_kernel (3 launches) Steps 2-6 in shared memory: cells of up to
 //                           1024 particles (4-warp teams), larger cells and
 //                           the pieces of big cells (8-warp teams)
@@ -559,7 +561,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.block_list = h->block_list;
   P.block_count = &h->ctl->block_count;
 
-  e = launch_big(P, h->mixed, h->sms, st);
+  e = launch_big(P, h->mixed, h->sms * 4, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);
   e = launch_team(P, h->mixed, 3, 1, h->cap_t, h->tiny_grid, st);

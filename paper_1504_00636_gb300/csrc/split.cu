@@ -1,12 +1,14 @@
-// big_kernel: cells larger than any shared-memory tile are cut (Sec. 3,
-// Steps 2-6) by a whole CTA in global memory, on the permutation array only,
-// until every piece fits; the pieces then go through the team kernel
-// (warp.cu).  Final sets met on the way are emitted here.
+// cluster_kernel: cells larger than any shared-memory tile are cut (Sec. 3,
+// Steps 2-6) by a thread-block cluster in global memory, on the permutation
+// array only, until every piece fits; the pieces then go through the team
+// kernel (warp.cu).  Final sets met on the way are emitted here.
 //
 // The CTA-per-cell building blocks below (a double-buffered shared-memory
 // tile, warp-level cuts of large subsets, thread-level depth-first finishing
 // of small ones) serve the allocation-free entry point at the end of this
 // file.
+#include <cooperative_groups.h>
+
 #include <cstddef>
 #include <mutex>
 
@@ -339,121 +341,206 @@ __device__ Moments<A, D> block_moments(const Problem &P, const int32_t *perm, in
   return R;
 }
 
+// The cluster-per-cell path.  A thread-block cluster of kClusterCtas CTAs
+// (512 threads each) takes one big cell at a time and cuts it (Steps 2-6)
+// in global memory, on the permutation only, until every piece fits one
+// CTA's tile; the pieces go to the team kernel.  For each set, CTA r of the
+// cluster handles the r-th contiguous chunk of the set's range: it sums the
+// chunk's moments and counts the chunk's V1 and V2 members, and the partial
+// sums and counts go to every CTA of the cluster through distributed shared
+// memory.  Every CTA merges the partials in rank order, so all take the same
+// decision; the chunks' V1 members are written to the front in chunk order
+// and their V2 members from the back, which is the order one CTA walking the
+// whole range would write.  Rank 0 keeps the cluster's stack of sets.
+constexpr int kClusterCtas = 4;
+constexpr int kClusterThreads = 256;
+
 template <typename T, int D>
-__global__ void __launch_bounds__(512) big_kernel(Problem P) {
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+    cluster_kernel(Problem P) {
+  namespace cg = cooperative_groups;
+  constexpr int K = kClusterCtas;
   constexpr int kStack = 1024;
-  __shared__ int4 stk[kStack];
-  __shared__ int s_sp, s_ticket;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  __shared__ int4 stk[kStack];  // rank 0: the cluster's pending sets
+  __shared__ int s_sp;
+  __shared__ int s_ticket;
+  __shared__ int4 s_item;       // the current set (written by rank 0)
   __shared__ __align__(16) BlockMoments<T, D> sh;
+  __shared__ __align__(16) Moments<double, D> s_part[K];  // partial sums by rank
+  __shared__ int s_cnt[K][3];   // V1 count, V2 count, near flag, by rank
   __shared__ int s_wcnt[2][16];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const unsigned lt = lanemask_lt();
-  if (timed_out(P.err)) return;
+  static_assert(sizeof(Moments<T, D>) == sizeof(Moments<double, D>), "partial slots");
+  if (timed_out(P.err)) return;  // the same in every CTA: set before the launch
   for (;;) {
-    __syncthreads();
-    if (tid == 0) s_ticket = atomicAdd(P.big_next, 1);
-    __syncthreads();
+    if (rank == 0 && tid == 0) {
+      const int t = atomicAdd(P.big_next, 1);
+      for (int r = 0; r < K; ++r) *cl.map_shared_rank(&s_ticket, r) = t;
+    }
+    cl.sync();
     const int t = s_ticket;
     if (t >= *P.big_count) break;
     const int c = P.big_list[t];
     const int64_t gb = P.cell_begin[c], ge = P.cell_begin[c + 1];
     if (*P.unsorted == 0)
-      for (int64_t i = gb + tid; i < ge; i += blockDim.x) P.perm[i] = (int32_t)i;
-    if (tid == 0) {
+      for (int64_t i = gb + (int64_t)rank * blockDim.x + tid; i < ge; i += (int64_t)K * blockDim.x)
+        P.perm[i] = (int32_t)i;
+    if (rank == 0 && tid == 0) {
       stk[0] = make_int4((int)gb, (int)ge, 0, c);
       s_sp = 1;
       atomicAdd(&P.stats[kStBig], 1ull);
       atomicAdd(&P.stats[kStCellsMerged], 1ull);
     }
-    __syncthreads();
-    while (s_sp > 0) {
-      __syncthreads();
-      const int4 it = stk[s_sp - 1];
-      __syncthreads();
-      if (tid == 0) --s_sp;
+    for (;;) {
+      cl.sync();  // perm up to date; the stack settled
+      if (rank == 0 && tid == 0) {
+        const int4 it = s_sp > 0 ? stk[--s_sp] : make_int4(-1, -1, 0, 0);
+        for (int r = 0; r < K; ++r) *cl.map_shared_rank(&s_item, r) = it;
+      }
+      cl.sync();
+      const int4 it = s_item;
+      if (it.x < 0) break;
       const int64_t b = it.x, e = it.y;
+      const int64_t m = e - b;
+      const int64_t c0 = b + m * rank / K, c1 = b + m * (rank + 1) / K;  // my chunk
       T s[D];
       const int first = P.perm[b];
 #pragma unroll
       for (int l = 0; l < D; ++l) s[l] = StoreOf<T>::load(P.q[l], first);
-      // Steps 2-6 on perm[b, e).  FP32 storage: a decision or a cut too close
-      // to call in FP32 is taken again with FP64 sums (exact = true); the
-      // control flow is the same in every thread (identical block sums).
-      const int mset = (int)(e - b);
+      // Steps 2-6 on perm[b, e).  FP32 storage: a decision or a cut too
+      // close to call in FP32 is taken again with FP64 sums (exact = true);
+      // the control flow is the same in every CTA (identical merged sums).
       bool exact = sizeof(T) == 8;
       Cut cut;
       int64_t nL = 0;
       for (;;) {
         bool bad = false;
+        // my chunk's moments, to every CTA's slot `rank`
         if (sizeof(T) == 4 && exact) {
           Moments<double, D> M = block_moments<double, T, D>(
-              P, P.perm, b, e, s, reinterpret_cast<BlockMoments<double, D> &>(sh), bad);
-          cut = decide_exact<T, D, true>(P, M, s, mset);
+              P, P.perm, c0, c1, s, reinterpret_cast<BlockMoments<double, D> &>(sh), bad);
+          if (tid == 0)
+            for (int r = 0; r < K; ++r) *cl.map_shared_rank(&s_part[rank], r) = M;
         } else {
-          Moments<T, D> M = block_moments<T, T, D>(P, P.perm, b, e, s, sh, bad);
-          const int64_t run = (e - b + blockDim.x - 1) / blockDim.x;
-          cut = Decider<T, D>::run(P, M, s, mset, run < 32 ? (int)run : 32);
+          Moments<T, D> M = block_moments<T, T, D>(P, P.perm, c0, c1, s, sh, bad);
+          if (tid == 0)
+            for (int r = 0; r < K; ++r)
+              *reinterpret_cast<Moments<T, D> *>(cl.map_shared_rank(&s_part[rank], r)) = M;
         }
         if (bad) set_error(P.err, kErrInput);
+        cl.sync();
+        if (sizeof(T) == 4 && exact) {
+          Moments<double, D> M = s_part[0];
+          for (int r = 1; r < K; ++r) M.merge(s_part[r]);
+          cut = decide_exact<T, D, true>(P, M, s, (int)m);
+        } else {
+          Moments<T, D> M = *reinterpret_cast<const Moments<T, D> *>(&s_part[0]);
+          for (int r = 1; r < K; ++r) M.merge(*reinterpret_cast<const Moments<T, D> *>(&s_part[r]));
+          cut = Decider<T, D>::run(P, M, s, (int)m, 32);
+        }
         if (cut.unsure) {
           exact = true;
-          if (tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
+          if (rank == 0 && tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
+          cl.sync();  // every CTA has read the partial slots
           continue;
         }
         unsigned ev = cut.near;
         nL = 0;
-        bool nr = false;
         if (!cut.leaf) {
-          // stable-left / reversed-right partition of perm[b, e) into perm_tmp
-          int64_t cntL = 0, cntR = 0;
-          for (int64_t base = b; base < e; base += blockDim.x) {
-            int64_t i = base + tid;
-            bool valid = i < e;
-            int src = valid ? P.perm[i] : 0;
-            const T q = StoreOf<T>::load(P.q[cut.k], src);
-            bool lft = valid && Decider<T, D>::left(q, cut);
-            nr |= valid && Decider<T, D>::near(q, cut);
-            unsigned bl = __ballot_sync(0xffffffffu, lft);
-            unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
+          // pass 1: my chunk's V1 and V2 counts and near band, to every CTA
+          int cl1 = 0, cr1 = 0;
+          bool nr = false;
+          for (int64_t i = c0 + tid; i < c1; i += blockDim.x) {
+            const T q = StoreOf<T>::load(P.q[cut.k], P.perm[i]);
+            if (Decider<T, D>::left(q, cut))
+              ++cl1;
+            else
+              ++cr1;
+            nr |= Decider<T, D>::near(q, cut);
+          }
+          cl1 = __reduce_add_sync(0xffffffffu, (unsigned)cl1);
+          cr1 = __reduce_add_sync(0xffffffffu, (unsigned)cr1);
+          __syncthreads();
+          if (lane == 0) {
+            s_wcnt[0][warp] = cl1;
+            s_wcnt[1][warp] = cr1;
+          }
+          const int anyn = __syncthreads_or(nr);
+          if (tid == 0) {
+            int L = 0, R = 0;
+            for (int k = 0; k < nw; ++k) {
+              L += s_wcnt[0][k];
+              R += s_wcnt[1][k];
+            }
+            for (int r = 0; r < K; ++r) {
+              int *dst = cl.map_shared_rank(&s_cnt[rank][0], r);
+              dst[0] = L;
+              dst[1] = R;
+              dst[2] = anyn;
+            }
+          }
+          cl.sync();
+          int64_t offL = 0, offR = 0, totL = 0;
+          bool gnear = false;
+          for (int r = 0; r < K; ++r) {
+            if (r < rank) {
+              offL += s_cnt[r][0];
+              offR += s_cnt[r][1];
+            }
+            totL += s_cnt[r][0];
+            gnear |= s_cnt[r][2] != 0;
+          }
+          if (gnear && !exact) {
+            exact = true;  // nothing written yet
+            if (rank == 0 && tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
+            continue;
+          }
+          if (gnear) ev |= kNearCut;
+          // pass 2: stable-left / reversed-right writes of my chunk into
+          // perm_tmp at the offsets of the earlier chunks
+          int64_t cntL = offL, cntR = offR;
+          for (int64_t base = c0; base < c1; base += blockDim.x) {
+            const int64_t i = base + tid;
+            const bool valid = i < c1;
+            const int src = valid ? P.perm[i] : 0;
+            const bool lft = valid && Decider<T, D>::left(StoreOf<T>::load(P.q[cut.k], src), cut);
+            const unsigned bl = __ballot_sync(0xffffffffu, lft);
+            const unsigned br = __ballot_sync(0xffffffffu, valid && !lft);
             __syncthreads();
             if (lane == 0) {
               s_wcnt[0][warp] = __popc(bl);
               s_wcnt[1][warp] = __popc(br);
             }
             __syncthreads();
-            int offL = 0, offR = 0, totL = 0, totR = 0;
+            int wL = 0, wR = 0, tL = 0, tR = 0;
             for (int k = 0; k < nw; ++k) {
               if (k < warp) {
-                offL += s_wcnt[0][k];
-                offR += s_wcnt[1][k];
+                wL += s_wcnt[0][k];
+                wR += s_wcnt[1][k];
               }
-              totL += s_wcnt[0][k];
-              totR += s_wcnt[1][k];
+              tL += s_wcnt[0][k];
+              tR += s_wcnt[1][k];
             }
             if (valid) {
-              int64_t dst = lft ? (b + cntL + offL + __popc(bl & lt))
-                                : (e - 1 - cntR - offR - __popc(br & lt));
+              const int64_t dst = lft ? (b + cntL + wL + __popc(bl & lt))
+                                      : (e - 1 - cntR - wR - __popc(br & lt));
               P.perm_tmp[dst] = src;
             }
-            cntL += totL;
-            cntR += totR;
+            cntL += tL;
+            cntR += tR;
           }
-          nr = __syncthreads_or(nr) != 0;
-          if (nr && !exact) {
-            exact = true;  // perm[b, e) is untouched until the copy below
-            if (tid == 0) atomicAdd(&P.stats[kStRecheck], 1ull);
-            continue;
-          }
-          if (nr) ev |= kNearCut;
-          for (int64_t i = b + tid; i < e; i += blockDim.x) P.perm[i] = P.perm_tmp[i];
-          nL = cntL;
-          if (cntL == 0 || cntR == 0) {
+          cl.sync();  // every chunk written
+          for (int64_t i = c0 + tid; i < c1; i += blockDim.x) P.perm[i] = P.perm_tmp[i];
+          nL = totL;
+          if (totL == 0 || totL == m) {
             cut.leaf = 1;
-            if (tid == 0) atomicAdd(&P.stats[kStDegenerate], 1ull);
+            if (rank == 0 && tid == 0) atomicAdd(&P.stats[kStDegenerate], 1ull);
           }
-          __syncthreads();
         }
-        if (ev && tid == 0) {
+        if (ev && rank == 0 && tid == 0) {
           if (ev & kNearStop) atomicAdd(&P.stats[kStNearStop], 1ull);
           if (ev & kNearArgmax) atomicAdd(&P.stats[kStNearArgmax], 1ull);
           if (ev & kNearCut) atomicAdd(&P.stats[kStNearCut], 1ull);
@@ -462,31 +549,31 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
         break;
       }
       if (cut.leaf) {
-        for (int64_t i = b + tid; i < e; i += blockDim.x) {
+        cl.sync();  // perm of the whole set copied back
+        for (int64_t i = c0 + tid; i < c1; i += blockDim.x) {
           P.perm_final[i] = P.perm[i];
-          P.head[i] = (i == b) ? head_code((int)(e - b)) : (uint8_t)0;
+          P.head[i] = (i == b) ? head_code((int)m) : (uint8_t)0;
           stage_global<T, D>(P, i, P.perm[i]);
         }
-        if (tid == 0) {
+        if (rank == 0 && tid == 0) {
           atomicAdd(&P.stats[kStLeaves], 1ull);
-          atomicAdd(&P.stats[kStDepth], (unsigned long long)it.z * (e - b));
+          atomicAdd(&P.stats[kStDepth], (unsigned long long)it.z * m);
         }
-        __syncthreads();
         continue;
       }
-      if (tid == 0) {
+      if (rank == 0 && tid == 0) {
         atomicAdd(&P.stats[kStSplits], 1ull);
-        int4 ch[2] = {make_int4((int)b, (int)(b + nL), it.z + 1, c),
-                      make_int4((int)(b + nL), (int)e, it.z + 1, c)};
+        const int4 ch[2] = {make_int4((int)b, (int)(b + nL), it.z + 1, c),
+                            make_int4((int)(b + nL), (int)e, it.z + 1, c)};
         for (int h = 1; h >= 0; --h) {
-          int n = ch[h].y - ch[h].x;
+          const int n = ch[h].y - ch[h].x;
           if (n > P.cap) {
             if (s_sp < kStack)
               stk[s_sp++] = ch[h];
             else
               set_error(P.err, kErrInternal);
           } else {
-            int slot = atomicAdd(P.piece_count, 1);
+            const int slot = atomicAdd(P.piece_count, 1);
             if (slot < P.max_pieces)
               P.pieces[slot] = ch[h];
             else
@@ -494,7 +581,6 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
           }
         }
       }
-      __syncthreads();
     }
   }
 }
@@ -503,7 +589,9 @@ __global__ void __launch_bounds__(512) big_kernel(Problem P) {
 
 template <typename T, int D>
 static cudaError_t launch_big_t(const Problem &P, int grid, cudaStream_t st) {
-  big_kernel<T, D><<<grid, 512, 0, st>>>(P);
+  // whole clusters only
+  grid = (grid + kClusterCtas - 1) / kClusterCtas * kClusterCtas;
+  cluster_kernel<T, D><<<grid, kClusterThreads, 0, st>>>(P);
   return cudaGetLastError();
 }
 
