@@ -63,6 +63,10 @@ def workload(name):
         return synth.two_stream()
     if name == "two_stream_small":
         return synth.two_stream(cells=1024)
+    if name == "two_stream_8k":
+        # 8192 cells (8.2M particles, 196 MB in float32): inputs larger than
+        # L2, for profiling captures
+        return synth.two_stream(cells=8192)
     if name == "two_stream_shuffled":
         return synth.two_stream().shuffled(3)
     if name == "shower":
