@@ -212,12 +212,15 @@ def alu_peaks():
                       "threads per SM, best of 5 launches (CUDA events)"}
 
 
-def time_device(p, mixed, steps, warmup, dev, flush, flags=0):
-    """K steps of one pma_merge each, inputs resident.  The step is captured
-    once into a CUDA graph and replayed; each replay is bracketed by CUDA
-    events on the capture stream (if capture fails, the same loop runs
-    eagerly).  Then K eager steps on the same stream are timed with the
-    library's per-stage events, which give the kernel durations."""
+def time_device(p, mixed, steps, warmup, dev, flush, flags=0, tune=True):
+    """K steps of one pma_merge each, inputs resident.  With `tune`, the
+    library's autotuner (pma_tune) first picks the population classes and the
+    class base on these particles, untimed, as a user would once per
+    workload shape.  The step is captured once into a CUDA graph and
+    replayed; each replay is bracketed by CUDA events on the capture stream
+    (if capture fails, the same loop runs eagerly).  Then K eager steps on
+    the same stream are timed with the library's per-stage events, which
+    give the kernel durations."""
     import torch
     from paper_1504_00636_gb300 import binding
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min,
@@ -226,6 +229,13 @@ def time_device(p, mixed, steps, warmup, dev, flush, flags=0):
     out = m.alloc_output(dev)
     stream = torch.cuda.Stream(dev)
     stream.wait_stream(torch.cuda.current_stream(dev))
+    default_classes = m.classes()
+    tune_s = None
+    if tune:
+        t0 = time.perf_counter()
+        m.tune(cells, pos, mom, w, p.tol_x, p.tol_p, out=out, stream=stream)
+        tune_s = round(time.perf_counter() - t0, 3)
+    classes = m.classes()
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             flush.fill_(1.0)
@@ -273,17 +283,28 @@ def time_device(p, mixed, steps, warmup, dev, flush, flags=0):
     m.close()
     del cells, pos, mom, w, out
     torch.cuda.empty_cache()
-    return dict(ms=ms, stage=stage, stats=st, M=M, graph=graph_ok, eager_ms=eager_ms)
+    return dict(ms=ms, stage=stage, stats=st, M=M, graph=graph_ok, eager_ms=eager_ms,
+                classes=classes, default_classes=default_classes, tune_s=tune_s)
 
 
-def time_e2e(p, mixed, steps, warmup):
+def classes_report(res):
+    """The team classes a run used: (cap_t, cap_w, cap, class base), whether
+    the tuner chose them, and how long tuning took."""
+    return {"used": list(res["classes"]), "default": list(res["default_classes"]),
+            "tuned": res["tune_s"] is not None, "tune_s": res["tune_s"]}
+
+
+def time_e2e(p, mixed, steps, warmup, classes=None):
     """Same metric through pma_merge_host: host->device copies of the inputs,
-    the merge, and device->host copies of the result inside the timed step."""
+    the merge, and device->host copies of the result inside the timed step
+    (with the classes the device run used)."""
     import torch
     from paper_1504_00636_gb300 import binding
     dt = np.float32 if mixed else np.float64
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, p.n_min,
                        "mixed" if mixed else "fp64")
+    if classes is not None:
+        m.set_classes(classes)
 
     def pinned(a):
         t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -495,11 +516,11 @@ def roofline(p, mixed, stats, stage_ms, peaks, peak_kind, M, workload_name, alu)
                                                           alu["source"]), **other}
 
 
-def extra_line(name, p, mixed, steps, warmup, dev, flush, peaks, flags=0):
-    """One more configuration, timed like the headline (graph replays, L2
-    flushed between steps): Mparticles/s, ms per call, step HBM fraction of
-    the algorithmic bytes, M and the per-stage times."""
-    res = time_device(p, mixed, steps, warmup, dev, flush, flags)
+def extra_line(name, p, mixed, steps, warmup, dev, flush, peaks, flags=0, tune=True):
+    """One more configuration, timed like the headline (tuned classes, graph
+    replays, L2 flushed between steps): Mparticles/s, ms per call, step HBM
+    fraction of the algorithmic bytes, M and the per-stage times."""
+    res = time_device(p, mixed, steps, warmup, dev, flush, flags, tune)
     t_ms = float(np.mean(res["ms"]))
     b_in, b_out = bytes_per_particle(p, mixed)
     step_bytes = p.n * (b_in + 4) + res["M"] * b_out
@@ -511,7 +532,8 @@ def extra_line(name, p, mixed, steps, warmup, dev, flush, peaks, flags=0):
             "fp64_rechecks": res["stats"]["fp64_rechecks"],
             "cells_flagged": res["stats"]["cells_flagged"],
             "cells_per_path": {k: res["stats"][k] for k in
-                               ("cells_tiny", "cells_small", "cells_large", "big_cells")}}
+                               ("cells_tiny", "cells_small", "cells_large", "big_cells")},
+            "classes": classes_report(res)}
 
 
 def main():
@@ -525,6 +547,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--classes", default="tuned", choices=["tuned", "default"],
+                    help="team classes: chosen by pma_tune on the workload (untimed), "
+                         "or the library's defaults")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other configurations (counter beams, shuffled and "
                          "momentum-norm two-stream, shower, 6D hot spots)")
@@ -582,7 +607,8 @@ def main():
     precs = {"both": [True, False], "mixed": [True], "fp64": [False]}[args.precision]
     for mixed in precs:
         q = p.astype(np.float32) if mixed else p
-        results[mixed] = time_device(q, mixed, args.steps, args.warmup, dev, flush)
+        results[mixed] = time_device(q, mixed, args.steps, args.warmup, dev, flush,
+                                     tune=args.classes == "tuned")
     barrier()
     clk = clocks.stop()
 
@@ -605,7 +631,7 @@ def main():
             depth_sum=res["stats"]["depth_sum"], splits=res["stats"]["splits"],
             fp64_rechecks=res["stats"]["fp64_rechecks"],
             cells_flagged=res["stats"]["cells_flagged"],
-            graph=res["graph"],
+            graph=res["graph"], classes=classes_report(res),
             eager_ms_per_step=round(float(np.mean(res["eager_ms"])), 4))
     head = lines[True] if True in lines else lines[False]
     mixed_head = True in lines
@@ -614,7 +640,8 @@ def main():
         # every rank copies its own replica in and out; the job takes the
         # slowest rank's time
         q = p.astype(np.float32) if mixed_head else p
-        e = time_e2e(q, mixed_head, max(3, args.steps // 4), 2)
+        e = time_e2e(q, mixed_head, max(3, args.steps // 4), 2,
+                     classes=results[mixed_head]["classes"])
         t_e2e = max_over_ranks(1e3 * float(np.mean(e["s"])), world, dev)
         e2e = {"value": round(job_throughput(p.n, 1, world, t_e2e), 2), "unit": UNIT,
                "h2d_bytes_per_step": e["h2d"] * world, "d2h_bytes_per_step": e["d2h"] * world}
@@ -629,12 +656,14 @@ def main():
             "cuda_graph": head["graph"], "eager_ms_per_step": head["eager_ms_per_step"],
             "gpu_launches": kernels_per_step(p.n_cells) * args.steps * len(lines),
             "clocks": clk, "alu_peaks": alu,
-            "fp64_rechecks": head["fp64_rechecks"], "cells_flagged": head["cells_flagged"]}
+            "fp64_rechecks": head["fp64_rechecks"], "cells_flagged": head["cells_flagged"],
+            "classes": head["classes"]}
     if mixed_head and False in lines:
         f = lines[False]
         line["fp64_plain"] = {"value": f["value"], "ms_per_step": f["ms_per_step"],
                               "cuda_graph": f["graph"], "eager_ms_per_step": f["eager_ms_per_step"],
                               "roofline": f["roofline"], "stage_ms": f["stage_ms"], "M": f["M"],
+                              "classes": f["classes"],
                               "speedup_mixed_over_fp64": round(head["value"] / f["value"], 3)}
     if e2e is not None:
         line["e2e"] = e2e
@@ -644,23 +673,26 @@ def main():
         from paper_1504_00636_gb300 import binding, synth
         ex = []
         K = max(3, min(args.steps, 10))
+        tune = args.classes == "tuned"
         cb = synth.counter_beams()
         for mx in (True, False):
             q = cb.astype(np.float32) if mx else cb
-            ex.append(extra_line("counter_beams (latency)", q, mx, K, 3, dev, flush, peaks))
+            ex.append(extra_line("counter_beams (latency)", q, mx, K, 3, dev, flush, peaks,
+                                 tune=tune))
         ts = synth.two_stream()
         sh = ts.shuffled(3).astype(np.float32)
-        ex.append(extra_line("two_stream shuffled", sh, True, K, 3, dev, flush, peaks))
+        ex.append(extra_line("two_stream shuffled", sh, True, K, 3, dev, flush, peaks,
+                             tune=tune))
         ex.append(extra_line("two_stream momentum-norm CV", ts.astype(np.float32), True, K, 3,
-                             dev, flush, peaks, binding.PMA_FLAG_MOMENTUM_NORM))
+                             dev, flush, peaks, binding.PMA_FLAG_MOMENTUM_NORM, tune=tune))
         del sh, ts
         shw = synth.shower()
         for mx in (True, False):
             q = shw.astype(np.float32) if mx else shw
-            ex.append(extra_line("shower", q, mx, K, 3, dev, flush, peaks))
+            ex.append(extra_line("shower", q, mx, K, 3, dev, flush, peaks, tune=tune))
         del shw, q
         h6 = synth.hot_6d()
-        ex.append(extra_line("hot_6d", h6, True, K, 3, dev, flush, peaks))
+        ex.append(extra_line("hot_6d", h6, True, K, 3, dev, flush, peaks, tune=tune))
         del h6
         line["other_configs"] = ex
     if mixed_head and not args.no_accuracy:

@@ -236,15 +236,21 @@ def pma_probe_fma(precision: str):
 
 
 def pma_get_classes(handle):
-    """(cap_t, cap_w, cap): the population limits of the one-warp, 4-warp and
-    8-warp team paths."""
-    c = (ctypes.c_int32 * 3)()
+    """(cap_t, cap_w, cap, base): the population limits of the one-warp,
+    4-warp and 8-warp team paths, and the class base of the subset size
+    classes."""
+    c = (ctypes.c_int32 * 4)()
     _check(load().pma_get_classes(handle, c), handle)
     return tuple(c)
 
 
 def pma_set_classes(handle, caps) -> None:
-    c = (ctypes.c_int32 * 3)(*caps)
+    """caps = (cap_t, cap_w, cap) keeps the handle's class base; a fourth
+    entry sets it."""
+    caps = tuple(caps)
+    if len(caps) == 3:
+        caps = caps + (pma_get_classes(handle)[3],)
+    c = (ctypes.c_int32 * 4)(*caps)
     _check(load().pma_set_classes(handle, c), handle)
 
 
@@ -256,13 +262,13 @@ def pma_tune(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_output,
 
 
 def pma_tune_cache_lookup(path: str, key: str):
-    c = (ctypes.c_int32 * 3)()
+    c = (ctypes.c_int32 * 4)()
     rc = load().pma_tune_cache_lookup(path.encode(), key.encode(), c)
     return tuple(c) if rc == PMA_OK else None
 
 
 def pma_tune_cache_store(path: str, key: str, caps, ms: float) -> None:
-    c = (ctypes.c_int32 * 3)(*caps)
+    c = (ctypes.c_int32 * 4)(*caps)
     _check(load().pma_tune_cache_store(path.encode(), key.encode(), c, float(ms)))
 
 
@@ -372,7 +378,8 @@ class Merger:
         return pma_get_stats(self.handle)
 
     def tune(self, cells, pos, mom, w, tol_x, tol_p, out: Output = None, stream=None):
-        """Time the population classes on these particles and keep the fastest."""
+        """Time the population classes and the class base on these particles and
+        keep the fastest; returns (cap_t, cap_w, cap, base)."""
         if out is None:
             out = self.alloc_output(cells.device)
         if stream is None:

@@ -79,6 +79,7 @@ struct pma_handle {
   int unit_grid = 0;
   int cap_w = 0;
   int cap_t = 0;
+  int class_base = kClassBaseMin;  // size classes of pending subsets
   int tiny_grid = 0;
   int warp_grid = 0;
   int64_t capacity = 0;
@@ -234,7 +235,7 @@ __global__ void zero_kernel(ZeroArgs z) {
 // first and their pieces join the 8-warp class.
 
 struct Classes {
-  int cap_t, cap_w, cap;
+  int cap_t, cap_w, cap, base;
 };
 
 // largest tile of at most `hi` particles whose team fits the CTA's shared memory
@@ -249,12 +250,14 @@ Classes default_classes(const pma_handle *h) {
   c.cap_w = largest_tile(h, 1024, 128);
   c.cap_t = 256;
   c.cap = largest_tile(h, 8191, c.cap_w);
+  c.base = kClassBaseMin;
   return c;
 }
 
 bool classes_valid(const pma_handle *h, const Classes &c) {
   return c.cap_t >= 2 && c.cap_t <= 1024 && c.cap_t <= c.cap_w && c.cap_w <= 1024 &&
-         c.cap_w <= c.cap && c.cap <= 8191 &&
+         c.cap_w <= c.cap && c.cap <= 8191 && c.base >= kClassBaseMin &&
+         c.base <= kClassBaseMax &&
          team_smem(h->mixed, h->D, c.cap) <= (size_t)h->smem_optin &&
          team_smem(h->mixed, h->D, c.cap_w) <= (size_t)h->smem_optin;
 }
@@ -266,6 +269,7 @@ void apply_classes(pma_handle *h, const Classes &c) {
   h->cap_t = c.cap_t;
   h->cap_w = c.cap_w;
   h->cap = c.cap;
+  h->class_base = c.base;
   h->warp_grid =
       h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap_w) + 1024)));
   // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
@@ -289,7 +293,7 @@ std::vector<Classes> class_candidates(const pma_handle *h) {
   for (int t : ts)
     for (int w : ws)
       for (int c : cs) {
-        Classes k{std::min(t, w), w, std::min(c, cmax)};
+        Classes k{std::min(t, w), w, std::min(c, cmax), kClassBaseMin};
         if (!classes_valid(h, k)) continue;
         bool dup = false;
         for (const Classes &o : v) dup |= o.cap_t == k.cap_t && o.cap_w == k.cap_w && o.cap == k.cap;
@@ -555,6 +559,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.warp_count = &h->ctl->warp_count;
   P.warp_next = &h->ctl->warp_next;
   P.cap_t = h->cap_t;
+  P.class_base = h->class_base;
   P.tiny_list = h->tiny_list;
   P.tiny_count = &h->ctl->tiny_count;
   P.tiny_next = &h->ctl->tiny_next;
@@ -697,17 +702,18 @@ int pma_get_stats(const pma_handle *h, pma_stats *out) {
 
 // ---------------------------------------------------------------- tuning
 
-int pma_get_classes(const pma_handle *h, int32_t caps[3]) {
+int pma_get_classes(const pma_handle *h, int32_t caps[4]) {
   if (!h || !caps) return PMA_ERR_INVALID_ARG;
   caps[0] = h->cap_t;
   caps[1] = h->cap_w;
   caps[2] = h->cap;
+  caps[3] = h->class_base;
   return PMA_OK;
 }
 
-int pma_set_classes(pma_handle *h, const int32_t caps[3]) {
+int pma_set_classes(pma_handle *h, const int32_t caps[4]) {
   if (!h || !caps) return PMA_ERR_INVALID_ARG;
-  const Classes c{caps[0], caps[1], caps[2]};
+  const Classes c{caps[0], caps[1], caps[2], caps[3]};
   if (!classes_valid(h, c)) return fail(h, PMA_ERR_INVALID_ARG, "invalid population classes");
   if (h->pending) {
     const int rc = pma_sync(h);
@@ -719,14 +725,16 @@ int pma_set_classes(pma_handle *h, const int32_t caps[3]) {
 
 namespace {
 
+constexpr int kCaps = 4;
+
 struct CacheEntry {
   std::string key;
-  int caps[3];
+  int caps[kCaps];
   double ms;
 };
 
 // the cache file: a JSON object, one entry per line,
-//   "key": [cap_t, cap_w, cap, ms],
+//   "key": [cap_t, cap_w, cap, base, ms],
 std::vector<CacheEntry> read_cache(const char *path) {
   std::vector<CacheEntry> v;
   FILE *f = fopen(path, "r");
@@ -741,7 +749,8 @@ std::vector<CacheEntry> read_cache(const char *path) {
     if (!br) continue;
     CacheEntry e;
     e.key.assign(a + 1, b);
-    if (sscanf(br + 1, "%d , %d , %d , %lf", &e.caps[0], &e.caps[1], &e.caps[2], &e.ms) == 4)
+    if (sscanf(br + 1, "%d , %d , %d , %d , %lf", &e.caps[0], &e.caps[1], &e.caps[2],
+               &e.caps[3], &e.ms) == 5)
       v.push_back(e);
   }
   fclose(f);
@@ -754,8 +763,8 @@ bool write_cache(const char *path, const std::vector<CacheEntry> &v) {
   if (!f) return false;
   fprintf(f, "{\n");
   for (size_t i = 0; i < v.size(); ++i)
-    fprintf(f, "  \"%s\": [%d, %d, %d, %.6g]%s\n", v[i].key.c_str(), v[i].caps[0],
-            v[i].caps[1], v[i].caps[2], v[i].ms, i + 1 < v.size() ? "," : "");
+    fprintf(f, "  \"%s\": [%d, %d, %d, %d, %.6g]%s\n", v[i].key.c_str(), v[i].caps[0],
+            v[i].caps[1], v[i].caps[2], v[i].caps[3], v[i].ms, i + 1 < v.size() ? "," : "");
   fprintf(f, "}\n");
   const bool ok = fclose(f) == 0;
   return ok && rename(tmp.c_str(), path) == 0;
@@ -763,30 +772,30 @@ bool write_cache(const char *path, const std::vector<CacheEntry> &v) {
 
 }  // namespace
 
-int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[3]) {
+int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[4]) {
   if (!path || !key || !caps) return PMA_ERR_INVALID_ARG;
   for (const CacheEntry &e : read_cache(path))
     if (e.key == key) {
-      for (int i = 0; i < 3; ++i) caps[i] = e.caps[i];
+      for (int i = 0; i < kCaps; ++i) caps[i] = e.caps[i];
       return PMA_OK;
     }
   return PMA_ERR_INVALID_ARG;
 }
 
-int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[3], double ms) {
+int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[4], double ms) {
   if (!path || !key || !caps || strchr(key, '"') || strchr(key, '\n')) return PMA_ERR_INVALID_ARG;
   std::vector<CacheEntry> v = read_cache(path);
   bool found = false;
   for (CacheEntry &e : v)
     if (e.key == key) {
-      for (int i = 0; i < 3; ++i) e.caps[i] = caps[i];
+      for (int i = 0; i < kCaps; ++i) e.caps[i] = caps[i];
       e.ms = ms;
       found = true;
     }
   if (!found) {
     CacheEntry e;
     e.key = key;
-    for (int i = 0; i < 3; ++i) e.caps[i] = caps[i];
+    for (int i = 0; i < kCaps; ++i) e.caps[i] = caps[i];
     e.ms = ms;
     v.push_back(e);
   }
@@ -814,7 +823,7 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
   snprintf(key, sizeof key, "D=%d %s flags=%u sms=%d %s", h->D, h->mixed ? "mixed" : "fp64",
            h->cfg.flags, h->sms, histogram_signature(counts).c_str());
   const char *cache = getenv("PMA_TUNE_CACHE");
-  int32_t caps[3];
+  int32_t caps[kCaps];
   if (cache && *cache && pma_tune_cache_lookup(cache, key, caps) == PMA_OK &&
       pma_set_classes(h, caps) == PMA_OK)
     return PMA_OK;
@@ -823,7 +832,8 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
   PMA_CUDA(h, cudaEventCreate(&e1));
   Classes best = default_classes(h);
   double best_ms = 1e300;
-  for (const Classes &c : class_candidates(h)) {
+  // median of three timed calls after one untimed
+  auto time_one = [&](const Classes &c) {
     apply_classes(h, c);
     float t[3];
     for (int r = -1; r < 3 && rc == PMA_OK; ++r) {
@@ -834,12 +844,24 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
       rc = pma_sync(h);
       if (r >= 0 && rc == PMA_OK) cudaEventElapsedTime(&t[r], e0, e1);
     }
-    if (rc != PMA_OK) break;
+    if (rc != PMA_OK) return;
     std::sort(t, t + 3);
     if (t[1] < best_ms) {
       best_ms = t[1];
       best = c;
     }
+  };
+  // the population limits with the default class base, then the class base
+  for (const Classes &c : class_candidates(h)) {
+    time_one(c);
+    if (rc != PMA_OK) break;
+  }
+  const Classes limits = best;
+  for (int b : {16, 24, 32}) {
+    if (rc != PMA_OK) break;
+    Classes c = limits;
+    c.base = b;
+    time_one(c);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -849,6 +871,7 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
     caps[0] = best.cap_t;
     caps[1] = best.cap_w;
     caps[2] = best.cap;
+    caps[3] = best.base;
     pma_tune_cache_store(cache, key, caps, best_ms);
   }
   return PMA_OK;

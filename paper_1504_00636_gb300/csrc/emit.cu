@@ -330,7 +330,7 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
 // CTA meanwhile reads the head bytes and scans them into output slots.  The
 // positions are then handled in consecutive order across the threads, so the
 // output stores of runs of one-particle sets are coalesced.
-template <typename T, bool EC>
+template <typename T, bool EC, bool EN>
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_bar;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     return;
   }
   bool bad = false, internal = false;
-  double ein = 0.0, eout = 0.0;  // kinetic energy in and out (a.energy only)
+  double ein = 0.0, eout = 0.0;  // kinetic energy in and out (EN only)
   int2 mg[kEmitChunk];           // this thread's merged heads: (offset, slot)
   unsigned mmask = 0u;
 #pragma unroll
@@ -425,13 +425,13 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
           bad |= !isfinite(v);
           const double q = to_f64<T>(v);
           a.out_mom[l][slot] = q;
-          if (a.energy) p2 = fma(q, q, p2);
+          if (EN) p2 = fma(q, q, p2);
         }
       }
       const T w = s_col[D * kEmitTile + off];
       bad |= !(w > T(0)) || !isfinite(w);
       a.out_w[slot] = to_f64<T>(w);
-      if (a.energy) {
+      if (EN) {
         const double k = kinetic(to_f64<T>(w), p2);
         ein += k;
         eout += k;
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
             S1[l] = fma(w, q, S1[l]);
             if (l >= a.dx) p2 = fma(q, q, p2);
           }
-        if (a.energy) ein += kinetic(w, p2);
+        if (EN) ein += kinetic(w, p2);
       }
     } else {
       for (int64_t r = t0 + off; r < e; ++r) {
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
             S1[l] = fma(w, q, S1[l]);
             if (l >= a.dx) p2 = fma(q, q, p2);
           }
-        if (a.energy) ein += kinetic(w, p2);
+        if (EN) ein += kinetic(w, p2);
       }
     }
     const double inv = 1.0 / W;
@@ -521,9 +521,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
         }
       }
     }
-    if (a.energy) eout += kinetic(W, P2);
+    if (EN) eout += kinetic(W, P2);
   }
-  if (a.energy) {
+  if (EN) {
     // kinetic energy in and out: block sums per tile, then the last CTA to
     // finish adds the tiles up in tile order (the same sum on every run)
 #pragma unroll
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
   if (internal) atomicOr(a.err, kErrInternal);
 }
 
-template <typename T, bool EC>
+template <typename T, bool EC, bool EN>
 static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   const size_t smem = emit_smem_bytes(a.dx + a.dp, sizeof(T) == 4);
   // raise the dynamic shared-memory limit once per device
@@ -571,12 +571,12 @@ static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
-    e = cudaFuncSetAttribute(emit_kernel<T, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(emit_kernel<T, EC, EN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
   }
-  emit_kernel<T, EC><<<a.tiles, kEmitThreads, smem, st>>>(a);
+  emit_kernel<T, EC, EN><<<a.tiles, kEmitThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -587,8 +587,18 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
   else
     count_kernel<false><<<a.tiles, kEmitThreads, 0, st>>>(a);
   tiles_kernel<<<1, kScanCta, 0, st>>>(a);
-  if (a.ec) return a.mixed ? launch_emit_t<float, true>(a, st) : launch_emit_t<double, true>(a, st);
-  return a.mixed ? launch_emit_t<float, false>(a, st) : launch_emit_t<double, false>(a, st);
+  // the energy sums are a separate build: they cost the plain path registers
+  const bool en = a.energy != nullptr;
+  if (a.ec) {
+    if (en) return a.mixed ? launch_emit_t<float, true, true>(a, st)
+                           : launch_emit_t<double, true, true>(a, st);
+    return a.mixed ? launch_emit_t<float, true, false>(a, st)
+                   : launch_emit_t<double, true, false>(a, st);
+  }
+  if (en) return a.mixed ? launch_emit_t<float, false, true>(a, st)
+                         : launch_emit_t<double, false, true>(a, st);
+  return a.mixed ? launch_emit_t<float, false, false>(a, st)
+                 : launch_emit_t<double, false, false>(a, st);
 }
 
 }  // namespace pma

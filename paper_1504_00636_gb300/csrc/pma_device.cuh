@@ -104,6 +104,9 @@ struct Problem {
   int32_t *tiny_next;
   int32_t *block_list;
   int32_t *block_count;
+  // size classes of pending subsets in the team kernels: pairs, then up to
+  // class_base particles, up to 2, 4, 8, 16 times class_base, and larger
+  int32_t class_base;
 };
 
 // ------------------------------------------------------------ accumulators

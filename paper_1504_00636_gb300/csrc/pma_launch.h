@@ -8,6 +8,13 @@
 
 namespace pma {
 
+// the class base B of the team kernels' subset size classes (the largest
+// subset a single lane takes) ranges over [kClassBaseMin, kClassBaseMax]: at
+// most 32 terms per lane in every class of a 1024-particle tile, and shared
+// memory is sized for the smallest B
+constexpr int kClassBaseMin = 12;
+constexpr int kClassBaseMax = 32;
+
 // split.cu
 size_t unit_smem(int mixed, int D, int cap);
 cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st);

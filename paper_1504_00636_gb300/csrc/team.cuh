@@ -12,8 +12,8 @@
 //
 // Pending subsets wait on one stack per size class.  A round takes up to
 // 32/G subsets of one class per warp and gives each a group of G lanes
-// (G = 32 for the largest sets down to G = 1, so that a lane reads a dozen
-// particles or so): moments by lane-strided sums and a butterfly inside the
+// (G = 32 for the largest sets down to G = 1, so that a lane reads at most
+// about B particles, B the class base of the handle: 12 by default): moments by lane-strided sums and a butterfly inside the
 // group, Steps 3-5, and the cut by group-masked ballots.  Two-particle sets
 // have their own round, the same arithmetic without loops.  CTA barriers
 // separate rounds.
@@ -36,29 +36,31 @@ constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
 constexpr int kMaxCapW = 8191;
 constexpr int kMaxTeam = 8;    // warps of the largest team
 
-// size class of a subset of m >= 2 particles
-__device__ __forceinline__ int size_class(int m) {
+// size class of a subset of m >= 2 particles for class base B: pairs, then
+// up to B, 2B, 4B, 8B, 16B particles, and more
+__device__ __forceinline__ int size_class(int m, int B) {
   if (m == 2) return 0;
-  if (m <= 12) return 1;
-  if (m <= 24) return 2;
-  if (m <= 48) return 3;
-  if (m <= 96) return 4;
-  if (m <= 192) return 5;
+  if (m <= B) return 1;
+  if (m <= 2 * B) return 2;
+  if (m <= 4 * B) return 3;
+  if (m <= 8 * B) return 4;
+  if (m <= 16 * B) return 5;
   return 6;
 }
 
 // most subsets of a class that can be pending at once: they are disjoint
 // subsets of at least lo particles of one tile of at most cap
-__host__ __device__ inline int class_capacity(int c, int cap) {
-  // smallest size of class c: 2, 3, 13, 25, 49, 97, 193
-  const int lo = c == 0 ? 2 : (c == 1 ? 3 : (12 << (c - 2)) + 1);
+__host__ __device__ inline int class_capacity(int c, int cap, int B = kClassBaseMin) {
+  // smallest size of class c: 2, 3, B + 1, 2B + 1, 4B + 1, 8B + 1, 16B + 1
+  const int lo = c == 0 ? 2 : (c == 1 ? 3 : (B << (c - 2)) + 1);
   return cap / lo;
 }
 
-// Pending pairs (n0) and 3-12-particle subsets (n1) are disjoint subsets of
-// the tile, so 2 n0 + 3 n1 <= cap and n0 + n1 <= cap / 2: the two classes
-// share one region of cap / 2 records, pairs from the front and the 3-12
-// class from the back.  Every other class has a region of its own.
+// Pending pairs (n0) and subsets of 3 to B particles (n1) are disjoint subsets
+// of the tile, so 2 n0 + 3 n1 <= cap and n0 + n1 <= cap / 2: the two classes
+// share one region of cap / 2 records, pairs from the front and the 3-B class
+// from the back.  Every other class has a region of its own (sized here for
+// the smallest B, which needs the most records).
 __host__ __device__ inline int stacks_entries(int cap) {
   int t = cap / 2;
   for (int c = 2; c < kClasses; ++c) t += class_capacity(c, cap);
@@ -88,6 +90,7 @@ struct WarpTile {
   const DecideConsts *dk;  // the FP64 decision's constants (for rechecks)
   void *wide;      // wide rounds: [kMaxTeam] partial moments, [kMaxTeam] counts
   int cap;
+  int base;        // class base B
   __device__ __forceinline__ T *col(int l) const { return data + (size_t)l * cap; }
   __device__ __forceinline__ uint16_t *idx(int par) const { return idx0 + par * cap; }
   // entry i of class c's stack (class 1 runs backwards from its region's end)
@@ -165,7 +168,7 @@ __device__ __forceinline__ unsigned push_set(unsigned *err, const WarpTile<T, D>
     mark_final<T, D>(S, b, S.idx(par)[b], kHeadSingle);
     return 1u;
   }
-  push_rec<T, D>(err, S, size_class(m), pack_rec(b, m, par));
+  push_rec<T, D>(err, S, size_class(m, S.base), pack_rec(b, m, par));
   return 0u;
 }
 
@@ -457,7 +460,7 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
   return kF ? __ballot_sync(full, redo && act && gl == 0) : 0u;
 }
 
-// A wide round: the (up to TEAM/2) pending sets of 193 or more particles,
+// A wide round: the (up to TEAM/2) pending sets of the largest class,
 // when they would leave warps idle, each get W = TEAM/2^k warps.
 // Moments: each warp sums a strided share, the W partial sums are merged in
 // warp order through shared memory.  Cut: warp u of the group takes the
@@ -738,6 +741,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       S.wide = base + woff;
     }
     S.cap = cap;
+    S.base = P.class_base;
     {
       const size_t doff = ((size_t)(static_cast<unsigned char *>(S.wide) - base) +
                            kMaxTeam * (sizeof(Moments<T, D>) + sizeof(int)) + 15) &
@@ -754,9 +758,9 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     }
     if (tt < kClasses) {
       int o = cap / 2;  // classes 0 and 1 share [0, cap / 2)
-      for (int c = 2; c < tt; ++c) o += class_capacity(c, cap);
+      for (int c = 2; c < tt; ++c) o += class_capacity(c, cap, S.base);
       S.soff[tt] = (uint16_t)(tt == 0 ? 0 : o);
-      S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap);
+      S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap, S.base);
     }
     if (tt < kEvWords) S.ev[tt] = 0;
   }
@@ -840,7 +844,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           emit_single<T, D>(P, S, perm, gb, 0, 0);
           cnt.leaves += 1;
         } else {
-          const int c = size_class(n);
+          const int c = size_class(n, S.base);
           *S.rec(c, 0) = pack_rec(0, n, 0);
           S.top[c] = 1;
         }
