@@ -259,17 +259,20 @@ int pma_test_status_of_bits(unsigned bits);
  *                    particles take one lane each, up to 2B two lanes, ...,
  *                    up to 16B sixteen lanes, larger ones a whole warp (or
  *                    several); pairs have a class of their own
+ *   caps[4] = widen  0 or 1: with 1, a round of a size class that has too
+ *                    few pending subsets to fill the team gives each subset
+ *                    more lanes (up to a warp)
  * with cap_t <= cap_w <= cap.  The result of a merge is the same for every
  * setting (every decision is exact up to the flagged near-ties); only the
- * time differs.  pma_create picks defaults (base 12); pma_set_classes sets
- * them (the next call uses them; PMA_ERR_INVALID_ARG when they are out of
+ * time differs.  pma_create picks defaults (base 12, widen 0);
+ * pma_set_classes sets them (the next call uses them; PMA_ERR_INVALID_ARG when they are out of
  * range) and pma_get_classes reads them.
  *
  * pma_tune times candidate settings on the caller's own particles (the
- * arguments as for pma_merge; at most the first 2^23 particles are used,
+ * arguments as for pma_merge; at most the first 2^26 particles are used,
  * so the input should be grouped by cell for the prefix to be whole cells):
  * first the population limits with base 12, then the base with the fastest
- * limits.  It keeps the fastest and synchronises, and writes the outputs as
+ * limits, then widen = 1 with the fastest base and with base 24.  It keeps the fastest and synchronises, and writes the outputs as
  * a merge of that prefix would.  When the environment variable
  * PMA_TUNE_CACHE names a file, the choice is looked up there first and
  * stored there afterwards under a key made of D, the precision, the flags,
@@ -277,17 +280,17 @@ int pma_test_status_of_bits(unsigned bits);
  * particles in cells of 1-64, 65-256, 257-1024, 1025-4096, 4097-8191 and
  * more particles, in twentieths).  The file is a JSON object with one entry
  * per line,
- *   "key": [cap_t, cap_w, cap, base, milliseconds],
+ *   "key": [cap_t, cap_w, cap, base, widen, milliseconds],
  * read and written with pma_tune_cache_lookup / pma_tune_cache_store (host
  * only; lookup returns PMA_ERR_INVALID_ARG when the key is absent).
  */
-int pma_get_classes(const pma_handle *h, int32_t caps[4]);
-int pma_set_classes(pma_handle *h, const int32_t caps[4]);
+int pma_get_classes(const pma_handle *h, int32_t caps[5]);
+int pma_set_classes(pma_handle *h, const int32_t caps[5]);
 int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *pos,
              const void *const *mom, const void *weights, double tol_x, double tol_p,
              const pma_output *out, void *stream);
-int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[4]);
-int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[4], double ms);
+int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[5]);
+int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[5], double ms);
 
 /* Wait for the handle's last enqueued call and return its device status. */
 int pma_sync(pma_handle *h);

@@ -236,21 +236,20 @@ def pma_probe_fma(precision: str):
 
 
 def pma_get_classes(handle):
-    """(cap_t, cap_w, cap, base): the population limits of the one-warp,
-    4-warp and 8-warp team paths, and the class base of the subset size
-    classes."""
-    c = (ctypes.c_int32 * 4)()
+    """(cap_t, cap_w, cap, base, widen): the population limits of the
+    one-warp, 4-warp and 8-warp team paths, the class base of the subset size
+    classes, and whether sparse rounds widen the lane groups."""
+    c = (ctypes.c_int32 * 5)()
     _check(load().pma_get_classes(handle, c), handle)
     return tuple(c)
 
 
 def pma_set_classes(handle, caps) -> None:
-    """caps = (cap_t, cap_w, cap) keeps the handle's class base; a fourth
-    entry sets it."""
+    """caps = (cap_t, cap_w, cap[, base[, widen]]); entries left out keep the
+    handle's current values."""
     caps = tuple(caps)
-    if len(caps) == 3:
-        caps = caps + (pma_get_classes(handle)[3],)
-    c = (ctypes.c_int32 * 4)(*caps)
+    caps = caps + pma_get_classes(handle)[len(caps):]
+    c = (ctypes.c_int32 * 5)(*caps)
     _check(load().pma_set_classes(handle, c), handle)
 
 
@@ -262,13 +261,13 @@ def pma_tune(handle, n, cells, pos, mom, weights, tol_x, tol_p, out: pma_output,
 
 
 def pma_tune_cache_lookup(path: str, key: str):
-    c = (ctypes.c_int32 * 4)()
+    c = (ctypes.c_int32 * 5)()
     rc = load().pma_tune_cache_lookup(path.encode(), key.encode(), c)
     return tuple(c) if rc == PMA_OK else None
 
 
 def pma_tune_cache_store(path: str, key: str, caps, ms: float) -> None:
-    c = (ctypes.c_int32 * 4)(*caps)
+    c = (ctypes.c_int32 * 5)(*caps)
     _check(load().pma_tune_cache_store(path.encode(), key.encode(), c, float(ms)))
 
 
@@ -378,8 +377,9 @@ class Merger:
         return pma_get_stats(self.handle)
 
     def tune(self, cells, pos, mom, w, tol_x, tol_p, out: Output = None, stream=None):
-        """Time the population classes and the class base on these particles and
-        keep the fastest; returns (cap_t, cap_w, cap, base)."""
+        """Time the population classes, the class base and group widening on
+        these particles and keep the fastest; returns
+        (cap_t, cap_w, cap, base, widen)."""
         if out is None:
             out = self.alloc_output(cells.device)
         if stream is None:

@@ -80,6 +80,7 @@ struct pma_handle {
   int cap_w = 0;
   int cap_t = 0;
   int class_base = kClassBaseMin;  // size classes of pending subsets
+  int widen_groups = 0;            // more lanes per set in sparse rounds
   int tiny_grid = 0;
   int warp_grid = 0;
   int64_t capacity = 0;
@@ -235,7 +236,7 @@ __global__ void zero_kernel(ZeroArgs z) {
 // first and their pieces join the 8-warp class.
 
 struct Classes {
-  int cap_t, cap_w, cap, base;
+  int cap_t, cap_w, cap, base, widen;
 };
 
 // largest tile of at most `hi` particles whose team fits the CTA's shared memory
@@ -251,13 +252,14 @@ Classes default_classes(const pma_handle *h) {
   c.cap_t = 256;
   c.cap = largest_tile(h, 8191, c.cap_w);
   c.base = kClassBaseMin;
+  c.widen = 0;
   return c;
 }
 
 bool classes_valid(const pma_handle *h, const Classes &c) {
   return c.cap_t >= 2 && c.cap_t <= 1024 && c.cap_t <= c.cap_w && c.cap_w <= 1024 &&
          c.cap_w <= c.cap && c.cap <= 8191 && c.base >= kClassBaseMin &&
-         c.base <= kClassBaseMax &&
+         c.base <= kClassBaseMax && (c.widen == 0 || c.widen == 1) &&
          team_smem(h->mixed, h->D, c.cap) <= (size_t)h->smem_optin &&
          team_smem(h->mixed, h->D, c.cap_w) <= (size_t)h->smem_optin;
 }
@@ -270,6 +272,7 @@ void apply_classes(pma_handle *h, const Classes &c) {
   h->cap_w = c.cap_w;
   h->cap = c.cap;
   h->class_base = c.base;
+  h->widen_groups = c.widen;
   h->warp_grid =
       h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap_w) + 1024)));
   // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
@@ -293,7 +296,7 @@ std::vector<Classes> class_candidates(const pma_handle *h) {
   for (int t : ts)
     for (int w : ws)
       for (int c : cs) {
-        Classes k{std::min(t, w), w, std::min(c, cmax), kClassBaseMin};
+        Classes k{std::min(t, w), w, std::min(c, cmax), kClassBaseMin, 0};
         if (!classes_valid(h, k)) continue;
         bool dup = false;
         for (const Classes &o : v) dup |= o.cap_t == k.cap_t && o.cap_w == k.cap_w && o.cap == k.cap;
@@ -560,6 +563,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.warp_next = &h->ctl->warp_next;
   P.cap_t = h->cap_t;
   P.class_base = h->class_base;
+  P.widen_groups = h->widen_groups;
   P.tiny_list = h->tiny_list;
   P.tiny_count = &h->ctl->tiny_count;
   P.tiny_next = &h->ctl->tiny_next;
@@ -702,18 +706,19 @@ int pma_get_stats(const pma_handle *h, pma_stats *out) {
 
 // ---------------------------------------------------------------- tuning
 
-int pma_get_classes(const pma_handle *h, int32_t caps[4]) {
+int pma_get_classes(const pma_handle *h, int32_t caps[5]) {
   if (!h || !caps) return PMA_ERR_INVALID_ARG;
   caps[0] = h->cap_t;
   caps[1] = h->cap_w;
   caps[2] = h->cap;
   caps[3] = h->class_base;
+  caps[4] = h->widen_groups;
   return PMA_OK;
 }
 
-int pma_set_classes(pma_handle *h, const int32_t caps[4]) {
+int pma_set_classes(pma_handle *h, const int32_t caps[5]) {
   if (!h || !caps) return PMA_ERR_INVALID_ARG;
-  const Classes c{caps[0], caps[1], caps[2], caps[3]};
+  const Classes c{caps[0], caps[1], caps[2], caps[3], caps[4]};
   if (!classes_valid(h, c)) return fail(h, PMA_ERR_INVALID_ARG, "invalid population classes");
   if (h->pending) {
     const int rc = pma_sync(h);
@@ -725,7 +730,7 @@ int pma_set_classes(pma_handle *h, const int32_t caps[4]) {
 
 namespace {
 
-constexpr int kCaps = 4;
+constexpr int kCaps = 5;
 
 struct CacheEntry {
   std::string key;
@@ -734,7 +739,7 @@ struct CacheEntry {
 };
 
 // the cache file: a JSON object, one entry per line,
-//   "key": [cap_t, cap_w, cap, base, ms],
+//   "key": [cap_t, cap_w, cap, base, widen, ms],
 std::vector<CacheEntry> read_cache(const char *path) {
   std::vector<CacheEntry> v;
   FILE *f = fopen(path, "r");
@@ -749,8 +754,8 @@ std::vector<CacheEntry> read_cache(const char *path) {
     if (!br) continue;
     CacheEntry e;
     e.key.assign(a + 1, b);
-    if (sscanf(br + 1, "%d , %d , %d , %d , %lf", &e.caps[0], &e.caps[1], &e.caps[2],
-               &e.caps[3], &e.ms) == 5)
+    if (sscanf(br + 1, "%d , %d , %d , %d , %d , %lf", &e.caps[0], &e.caps[1], &e.caps[2],
+               &e.caps[3], &e.caps[4], &e.ms) == 6)
       v.push_back(e);
   }
   fclose(f);
@@ -763,8 +768,9 @@ bool write_cache(const char *path, const std::vector<CacheEntry> &v) {
   if (!f) return false;
   fprintf(f, "{\n");
   for (size_t i = 0; i < v.size(); ++i)
-    fprintf(f, "  \"%s\": [%d, %d, %d, %d, %.6g]%s\n", v[i].key.c_str(), v[i].caps[0],
-            v[i].caps[1], v[i].caps[2], v[i].caps[3], v[i].ms, i + 1 < v.size() ? "," : "");
+    fprintf(f, "  \"%s\": [%d, %d, %d, %d, %d, %.6g]%s\n", v[i].key.c_str(), v[i].caps[0],
+            v[i].caps[1], v[i].caps[2], v[i].caps[3], v[i].caps[4], v[i].ms,
+            i + 1 < v.size() ? "," : "");
   fprintf(f, "}\n");
   const bool ok = fclose(f) == 0;
   return ok && rename(tmp.c_str(), path) == 0;
@@ -772,7 +778,7 @@ bool write_cache(const char *path, const std::vector<CacheEntry> &v) {
 
 }  // namespace
 
-int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[4]) {
+int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[5]) {
   if (!path || !key || !caps) return PMA_ERR_INVALID_ARG;
   for (const CacheEntry &e : read_cache(path))
     if (e.key == key) {
@@ -782,7 +788,7 @@ int pma_tune_cache_lookup(const char *path, const char *key, int32_t caps[4]) {
   return PMA_ERR_INVALID_ARG;
 }
 
-int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[4], double ms) {
+int pma_tune_cache_store(const char *path, const char *key, const int32_t caps[5], double ms) {
   if (!path || !key || !caps || strchr(key, '"') || strchr(key, '\n')) return PMA_ERR_INVALID_ARG;
   std::vector<CacheEntry> v = read_cache(path);
   bool found = false;
@@ -809,8 +815,8 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
   if (rc != PMA_OK) return rc;
   if (n == 0) return PMA_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // a prefix of the input (at most 2^23 particles) stands for the whole
-  const int64_t ns = std::min<int64_t>(n, (int64_t)1 << 23);
+  // a prefix of the input (at most 2^26 particles) stands for the whole
+  const int64_t ns = std::min<int64_t>(n, (int64_t)1 << 26);
   pma_output o = *out;
   o.cell_flags = nullptr;
   int64_t M = 0;
@@ -863,6 +869,17 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
     c.base = b;
     time_one(c);
   }
+  // then wider groups in sparse rounds, with the best class base and with
+  // base 24 (their best partner on the measured workloads)
+  const Classes narrow = best;
+  for (int b : {narrow.base, 24}) {
+    if (rc != PMA_OK) break;
+    if (b == 24 && narrow.base == 24) continue;
+    Classes c = narrow;
+    c.base = b;
+    c.widen = 1;
+    time_one(c);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   apply_classes(h, best);
@@ -872,6 +889,7 @@ int pma_tune(pma_handle *h, int64_t n, const int32_t *cells, const void *const *
     caps[1] = best.cap_w;
     caps[2] = best.cap;
     caps[3] = best.base;
+    caps[4] = best.widen;
     pma_tune_cache_store(cache, key, caps, best_ms);
   }
   return PMA_OK;

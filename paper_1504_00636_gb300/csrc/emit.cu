@@ -24,6 +24,7 @@ namespace pma {
 constexpr int kEmitThreads = 256;
 constexpr int kEmitChunk = 4;  // consecutive positions per thread
 constexpr int kEmitTile = kEmitThreads * kEmitChunk;
+constexpr int kWarpSet = 32;  // merged sets of at least this many members: one warp each
 constexpr int kScanCta = 1024;
 
 int emit_tiles_for(int64_t n) { return (int)((n + kEmitTile - 1) / kEmitTile); }
@@ -330,8 +331,17 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
 // CTA meanwhile reads the head bytes and scans them into output slots.  The
 // positions are then handled in consecutive order across the threads, so the
 // output stores of runs of one-particle sets are coalesced.
+// CTAs per SM the plain builds are held to (float: at most 42 registers,
+// shared memory allows 7; FP64: at most 64, shared memory allows 4); the
+// energy-conserving and energy-accounting builds take the registers they need
 template <typename T, bool EC, bool EN>
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
+constexpr int emit_min_blocks() {
+  return (EC || EN) ? 1 : (sizeof(T) == 4 ? 6 : 4);
+}
+
+template <typename T, bool EC, bool EN>
+__global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
+    emit_kernel(EmitArgs a) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_warp[32];
@@ -457,6 +467,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
     const int off = s_merged[k].x;
     const long long slot_m = s_merged[k].y;
     const int h = s_head[off];
+    if (!EC && h >= kWarpSet) continue;  // summed by a warp below
     // members: the head's count, or (255) every position up to the next head
     int64_t e = t0 + off + h;
     if (h == kHeadLong) {
@@ -522,6 +533,82 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(EmitArgs a) {
       }
     }
     if (EN) eout += kinetic(W, P2);
+  }
+  if (!EC) {
+    // sets of kWarpSet or more members: one warp each, lane-strided FP64
+    // sums and a fixed butterfly (the same order on every run)
+    const unsigned full = 0xffffffffu;
+    const int lane = tid & 31;
+    for (int k = tid >> 5; k < s_nmerged; k += kEmitThreads / 32) {
+      const int off = s_merged[k].x;
+      const int h = s_head[off];
+      if (h < kWarpSet) continue;  // warp-uniform
+      const long long slot_m = s_merged[k].y;
+      int64_t e = t0 + off + h;
+      if (h == kHeadLong) {
+        // the next head (or the end), 32 head bytes per step
+        int64_t from = t0 + off + 1;
+        for (;;) {
+          const int64_t i = from + lane;
+          const bool hd = i >= a.n || (i < t0 + cnt ? s_head[i - t0] : a.head[i]) != 0;
+          const unsigned bh = __ballot_sync(full, hd);
+          if (bh) {
+            e = from + __ffs(bh) - 1;
+            break;
+          }
+          from += 32;
+        }
+      }
+      if (e > a.n) {
+        internal = true;
+        e = a.n;
+      }
+      double W = 0.0, S1[kMaxD];
+#pragma unroll
+      for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
+      for (int64_t r = t0 + off + lane; r < e; r += 32) {
+        const bool here = r < t0 + cnt;
+        const int rl = (int)(r - t0);
+        const double w = to_f64<T>(here ? s_col[D * kEmitTile + rl]
+                                        : static_cast<const T *>(a.fin[D])[r]);
+        W += w;
+        double p2 = 0.0;
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) {
+            const double q = to_f64<T>(here ? s_col[l * kEmitTile + rl]
+                                            : static_cast<const T *>(a.fin[l])[r]);
+            S1[l] = fma(w, q, S1[l]);
+            if (l >= a.dx) p2 = fma(q, q, p2);
+          }
+        if (EN) ein += kinetic(w, p2);
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        W += __shfl_xor_sync(full, W, o);
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) S1[l] += __shfl_xor_sync(full, S1[l], o);
+      }
+      if (lane == 0) {
+        const double inv = 1.0 / W;
+        a.out_w[slot_m] = W;
+        double P2 = 0.0;
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l) {
+          if (l < D) {
+            const double v = S1[l] * inv;
+            if (l < 3 && l < a.dx) {
+              static_cast<T *>(a.out_pos[l])[slot_m] = (T)v;
+            } else {
+              a.out_mom[l - a.dx][slot_m] = v;
+              P2 = fma(v, v, P2);
+            }
+          }
+        }
+        if (EN) eout += kinetic(W, P2);
+      }
+    }
   }
   if (EN) {
     // kinetic energy in and out: block sums per tile, then the last CTA to

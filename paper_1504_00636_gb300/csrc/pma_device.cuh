@@ -107,6 +107,9 @@ struct Problem {
   // size classes of pending subsets in the team kernels: pairs, then up to
   // class_base particles, up to 2, 4, 8, 16 times class_base, and larger
   int32_t class_base;
+  // nonzero: a round of a size class with few pending subsets gives each
+  // more lanes (up to a warp) instead of leaving warps of the team idle
+  int32_t widen_groups;
 };
 
 // ------------------------------------------------------------ accumulators

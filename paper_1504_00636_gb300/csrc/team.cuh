@@ -340,16 +340,17 @@ __device__ __forceinline__ void exact_sets(const Problem &P, const WarpTile<T, D
   }
 }
 
-// one round of class c >= 1 for this warp: kw <= 32/G subsets, G lanes
-// each; rec is the record of the lane's group (read before the round).
+// one round of a class c >= 1 for this warp: kw <= 32/G subsets, G = 2^lg
+// lanes each (G >= 2^(c-1)); rec is the record of the lane's group (read
+// before the round).
 // Returns the lanes whose set needs the FP64 recheck (exact_sets).
 template <typename T, int D, bool VAR, int TEAM>
 __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
-                                int64_t gb, int c, int lane, Counters &cnt, int kw,
+                                int64_t gb, int lg, int lane, Counters &cnt, int kw,
                                 uint32_t rec) {
   constexpr bool kF = sizeof(T) == 4;
   const unsigned full = 0xffffffffu;
-  const int lg = c - 1, G = 1 << lg;
+  const int G = 1 << lg;
   const int gid = lane >> lg, gl = lane & (G - 1);
   const bool act = gid < kw;
   const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
@@ -878,13 +879,19 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
             exact_sets<T, D, VAR>(P, S, 1u, rec, lane, cnt);
           continue;
         }
-        const int per = (c == 0) ? 32 : (32 >> (c - 1));
+        // G = 2^lg lanes per set: the class's own, or (when the handle asks
+        // for it) more while the team still takes every pending set of the
+        // class in this round
+        int lg = c == 0 ? 0 : c - 1;
+        if (c >= 1 && P.widen_groups)
+          while (lg < 5 && TEAM * (32 >> (lg + 1)) >= avail) ++lg;
+        const int per = 32 >> lg;
         const int k = min(avail, TEAM * per);
         const int kw = max(0, min(per, k - wt * per));
         const int base = avail - 1 - wt * per;
         uint32_t rec = 0u;
         if (kw > 0) {
-          const int gid = c <= 1 ? lane : (lane >> (c - 1));
+          const int gid = lane >> lg;
           if (gid < kw) rec = *S.rec(c, base - gid);
         }
         __syncthreads();
@@ -895,7 +902,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           if (c == 0)
             pend = pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, rec);
           else
-            pend = group_round<T, D, VAR, TEAM>(P, S, perm, gb, c, lane, cnt, kw, rec);
+            pend = group_round<T, D, VAR, TEAM>(P, S, perm, gb, lg, lane, cnt, kw, rec);
           // FP32 storage: the rare FP64 rechecks, by the whole warp, after
           // its share of the round
           if (sizeof(T) == 4 && pend) exact_sets<T, D, VAR>(P, S, pend, rec, lane, cnt);

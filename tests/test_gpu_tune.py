@@ -1,7 +1,8 @@
-"""The autotuner on the GPU: it picks valid population classes and a valid
-class base, the result of a merge depends on neither (every decision is exact
-up to flagged near-ties, so cells give the same sets on every path and in
-every size class), and its choice is cached under PMA_TUNE_CACHE."""
+"""The autotuner on the GPU: it picks valid population classes, class base
+and group widening, the result of a merge depends on none of them (every
+decision is exact up to flagged near-ties, so cells give the same sets on
+every path, in every size class and with any number of lanes per set), and
+its choice is cached under PMA_TUNE_CACHE."""
 import json
 
 import numpy as np
@@ -34,9 +35,9 @@ def test_classes_do_not_change_the_result(precision):
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, precision)
     base = run_gpu(p, precision, merger=m)
     default = m.classes()
-    for caps in [(128, 512, 2048, 12), (512, 1024, 4096, 16), (64, 256, 1024, 24),
-                 (256, 1024, 8191, 32)]:
-        caps = (caps[0], caps[1], min(caps[2], default[2]), caps[3])
+    for caps in [(128, 512, 2048, 12, 0), (512, 1024, 4096, 16, 1), (64, 256, 1024, 24, 0),
+                 (256, 1024, 8191, 32, 1), (256, 1024, 8191, 12, 1)]:
+        caps = (caps[0], caps[1], min(caps[2], default[2]), caps[3], caps[4])
         m.set_classes(caps)
         assert m.classes() == caps
         g = run_gpu(p, precision, merger=m)
@@ -56,7 +57,9 @@ def test_classes_do_not_change_the_result(precision):
         m.set_classes((256, 1024, 100000))
     for bad_base in (11, 33):
         with pytest.raises(binding.PmaError):
-            m.set_classes((256, 1024, 2048, bad_base))
+            m.set_classes((256, 1024, 2048, bad_base, 0))
+    with pytest.raises(binding.PmaError):
+        m.set_classes((256, 1024, 2048, 12, 2))
     m.set_classes(default)
     assert m.classes() == default
     m.close()
@@ -70,14 +73,14 @@ def test_tune_picks_valid_classes_and_caches_them(tmp_path, monkeypatch):
     cells, pos, mom, w = _inputs(p, True)
     m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, "mixed")
     caps = m.tune(cells, pos, mom, w, p.tol_x, p.tol_p)
-    assert caps[0] <= caps[1] <= caps[2] <= 8191 and 12 <= caps[3] <= 32
+    assert caps[0] <= caps[1] <= caps[2] <= 8191 and 12 <= caps[3] <= 32 and caps[4] in (0, 1)
     d = json.load(open(path))
     assert len(d) == 1
     key, val = next(iter(d.items()))
-    assert key.startswith("D=5 mixed flags=0") and tuple(val[:4]) == caps
+    assert key.startswith("D=5 mixed flags=0") and tuple(val[:5]) == caps
     # a second handle finds the entry and takes it
     m2 = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, "mixed")
-    m2.set_classes((64, 256, 1024, 20))
+    m2.set_classes((64, 256, 1024, 20, 1))
     assert m2.tune(cells, pos, mom, w, p.tol_x, p.tol_p) == caps
     # the tuned handle gives the untuned handle's result
     g = run_gpu(p, "mixed", merger=m)
