@@ -40,11 +40,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 
 def kernels_per_step(n_cells):
     """Library kernels one merge call launches: the clearing kernel, hist,
-    scan, radix prep, one radix pass per 8-bit digit of the cell id (these
-    return at once on grouped input), big-cell cuts, four team launches
-    (tiny, small, large cells, pieces), count, tiles, emit."""
+    scan, radix prep, one radix pass per 8-bit digit of the cell id and the
+    sorted-order copy (these return at once on grouped input), big-cell
+    cuts, four team launches (tiny, small, large cells, pieces), count,
+    tiles, emit."""
     bits = max(1, int(n_cells).bit_length())
-    return 1 + 2 + 1 + (bits + 7) // 8 + 1 + 4 + 3
+    return 1 + 2 + 1 + (bits + 7) // 8 + 1 + 1 + 4 + 3
 
 
 def load_peaks():

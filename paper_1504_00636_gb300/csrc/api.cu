@@ -513,7 +513,6 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   mark(h, 0, st);
   cudaError_t e = launch_binning(b, h->sms, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "binning launch");
-  mark(h, 1, st);
 
   Problem P{};
   P.n_cells = (int32_t)C;
@@ -570,6 +569,9 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.block_list = h->block_list;
   P.block_count = &h->ctl->block_count;
 
+  e = launch_gather(P, n, h->mixed, h->sms, st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "gather launch");
+  mark(h, 1, st);  // Step 1 done: binned (and, for ungrouped input, copied in sorted order)
   e = launch_big(P, h->mixed, h->sms * 4, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);

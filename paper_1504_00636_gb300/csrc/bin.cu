@@ -1,8 +1,9 @@
 // Step 1 of the method: collect the particles of every simulation cell.
 //
-// hist_kernel   validates the cell ids, counts particles per cell (warp-
-//               aggregated atomics) and detects input that is already
-//               grouped by cell (non-decreasing ids).
+// hist_kernel   validates the cell ids, counts particles per cell (one
+//               atomic per run of equal ids, in shared memory when the cells
+//               are few) and detects input that is already grouped by cell
+//               (non-decreasing ids).
 // scan_kernel   exclusive prefix of the counts -> first sorted position of
 //               every cell (single pass, decoupled look-back), and the list of
 //               cells too large for one CTA's shared memory.
@@ -32,8 +33,19 @@ constexpr int kHistRows = 4;  // rows of 32 ids a warp loads per step
 // one atomic (run starts from a neighbour shuffle and one ballot), so ids
 // grouped by cell cost one atomic per run; ungrouped ids stay correct (runs
 // of one).  A pair of neighbours in decreasing order marks the input as not
-// grouped.
-__global__ void __launch_bounds__(256) hist_kernel(BinArgs a) {
+// grouped.  With few cells (SMEM) the CTA counts in shared memory and adds
+// its non-zero counts to the global ones at the end: ungrouped ids then cost
+// one global atomic per cell and CTA instead of one per particle.
+constexpr int kHistSmemCells = 12288;  // 48 KB of shared counters
+constexpr int kHistSmemThreads = 1024;
+
+template <bool SMEM>
+__global__ void __launch_bounds__(SMEM ? kHistSmemThreads : 256) hist_kernel(BinArgs a) {
+  extern __shared__ int s_count[];  // SMEM: [n_cells]
+  if (SMEM) {
+    for (int k = threadIdx.x; k < a.n_cells; k += blockDim.x) s_count[k] = 0;
+    __syncthreads();
+  }
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -66,12 +78,17 @@ __global__ void __launch_bounds__(256) hist_kernel(BinArgs a) {
       if (start && key >= 0) {
         const unsigned later = starts & ~((2u << lane) - 1u);
         const int end = later ? __ffs(later) - 1 : 32;
-        atomicAdd(&a.counts[key], end - lane);
+        atomicAdd(SMEM ? &s_count[key] : &a.counts[key], end - lane);
       }
     }
   }
   if (__any_sync(full, bad) && lane == 0) atomicOr(a.err, kErrInput);
   if (__any_sync(full, unsorted) && lane == 0) atomicExch(a.unsorted, 1);
+  if (SMEM) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_cells; k += blockDim.x)
+      if (s_count[k]) atomicAdd(&a.counts[k], s_count[k]);
+  }
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(BinArgs a) {
@@ -254,11 +271,65 @@ __global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, in
   }
 }
 
+// Ungrouped input only (returns at once otherwise): every particle's
+// coordinates and weight in sorted (cell, input index) order, copied into
+// the staging columns, so that the partition kernels read each cell
+// contiguously instead of gathering it through the permutation (they later
+// overwrite the columns of a cell with its final order).  One sorted
+// position per thread and step: the permutation and the stores are
+// coalesced, the loads scattered.
+constexpr int kGatherUnroll = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(Problem P, int64_t n) {
+  if (*P.unsorted == 0 || timed_out(P.err)) return;
+  const int D = P.D;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n;
+       i0 += stride * kGatherUnroll) {
+    int src[kGatherUnroll];
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      src[u] = i < n ? P.perm[i] : -1;
+      if ((unsigned)src[u] >= (unsigned)n) src[u] = -1;  // never after a complete sort
+    }
+#pragma unroll
+    for (int l = 0; l <= kMaxD; ++l) {
+      if (l > D) break;
+      const T *col = static_cast<const T *>(l < D ? P.q[l] : P.w);
+      T v[kGatherUnroll];
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u) v[u] = src[u] >= 0 ? col[src[u]] : T(0);
+#pragma unroll
+      for (int u = 0; u < kGatherUnroll; ++u)
+        if (src[u] >= 0) static_cast<T *>(P.fin[l])[i0 + u * stride] = v[u];
+    }
+  }
+}
+
+cudaError_t launch_gather(const Problem &P, int64_t n, int mixed, int sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  if (mixed)
+    gather_kernel<float><<<grid, 256, 0, st>>>(P, n);
+  else
+    gather_kernel<double><<<grid, 256, 0, st>>>(P, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st) {
   if (a.n > 0) {
-    int grid = (int)std::min<int64_t>((a.n + 256 * kHistRows - 1) / (256 * kHistRows),
-                                      (int64_t)sms * 8);
-    hist_kernel<<<grid, 256, 0, st>>>(a);
+    if (a.n_cells <= kHistSmemCells) {
+      const int grid = (int)std::min<int64_t>(
+          (a.n + kHistSmemThreads * kHistRows - 1) / (kHistSmemThreads * kHistRows),
+          (int64_t)sms * 2);
+      hist_kernel<true><<<grid, kHistSmemThreads, (size_t)a.n_cells * sizeof(int), st>>>(a);
+    } else {
+      const int grid = (int)std::min<int64_t>((a.n + 256 * kHistRows - 1) / (256 * kHistRows),
+                                              (int64_t)sms * 8);
+      hist_kernel<false><<<grid, 256, 0, st>>>(a);
+    }
   }
   scan_kernel<<<a.scan_tiles, kScanThreads, 0, st>>>(a);
   if (a.n > 0) {

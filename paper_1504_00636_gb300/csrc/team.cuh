@@ -766,6 +766,11 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     if (tt < kEvWords) S.ev[tt] = 0;
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
+  // ungrouped input: the cells' particles were copied in sorted order into
+  // the staging columns (gather_kernel), so a cell reads them contiguously;
+  // pieces of big cells still read the inputs through the permutation
+  // (recomputed where needed rather than held in a register)
+#define PMA_SORTED_COPY (perm != nullptr && U.mode != 2)
   const int chunk = (U.mode == 0 || U.mode == 3) ? kWarpChunk : 1;
   Counters cnt{0u, 0u, 0u, 0ull};
   unsigned long long merged = 0, passed = 0;
@@ -791,10 +796,12 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           const int src = orig_index(perm, gb, i);
           P.perm_final[gb + i] = src;
           P.head[gb + i] = kHeadSingle;
+          if (!PMA_SORTED_COPY) {  // (the sorted copy already sits there)
 #pragma unroll
-          for (int l = 0; l < D; ++l)
-            static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
-          static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+            for (int l = 0; l < D; ++l)
+              static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
+            static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+          }
         }
         passed += 1;
         continue;
@@ -805,14 +812,15 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       }
       if (U.mode != 2) merged += 1;
       if (tt == 0) cnt.depth += (unsigned long long)depth0 * n;
-      if (t + 1 < c1 && !perm && tt < D + 1) {
+      if (t + 1 < c1 && (!perm || PMA_SORTED_COPY) && tt < D + 1) {
         // the next unit of this chunk: pull its columns into L2 meanwhile
         int64_t nb;
         int nn, nd, nc;
         unit_at(P, U, t + 1, nb, nn, nd, nc);
         const int64_t ne = nb + nn;
         const size_t es = sizeof(T);
-        const char *col = static_cast<const char *>(tt < D ? P.q[tt] : P.w);
+        const char *col = static_cast<const char *>(
+            PMA_SORTED_COPY ? P.fin[tt] : (tt < D ? P.q[tt] : P.w));
         // the 16-byte-aligned part of the range only: never outside the array
         const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nb * es) + 15) & ~uintptr_t(15);
         const uintptr_t a1 = (reinterpret_cast<uintptr_t>(col + ne * es)) & ~uintptr_t(15);
@@ -822,19 +830,32 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
                        : "memory");
       }
       bool bad = false;
+      if (PMA_SORTED_COPY) {
 #pragma unroll 4
-      for (int i = tt; i < n; i += kThreads) {
-        const int src = orig_index(perm, gb, i);
+        for (int i = tt; i < n; i += kThreads) {
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const T x = StoreOf<T>::load(P.q[l], src);
-          bad |= !finite_val(x);
-          S.col(l)[i] = x;
+          for (int l = 0; l <= D; ++l) {
+            const T x = static_cast<const T *>(P.fin[l])[gb + i];
+            bad |= l < D ? !finite_val(x) : (!(x > T(0)) || !finite_val(x));
+            S.col(l)[i] = x;
+          }
+          S.idx(0)[i] = (uint16_t)i;
         }
-        const T w = StoreOf<T>::load(P.w, src);
-        bad |= !(w > T(0)) || !finite_val(w);
-        S.col(D)[i] = w;
-        S.idx(0)[i] = (uint16_t)i;
+      } else {
+#pragma unroll 4
+        for (int i = tt; i < n; i += kThreads) {
+          const int src = orig_index(perm, gb, i);
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const T x = StoreOf<T>::load(P.q[l], src);
+            bad |= !finite_val(x);
+            S.col(l)[i] = x;
+          }
+          const T w = StoreOf<T>::load(P.w, src);
+          bad |= !(w > T(0)) || !finite_val(w);
+          S.col(D)[i] = w;
+          S.idx(0)[i] = (uint16_t)i;
+        }
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
       if (tt < kClasses) S.top[tt] = 0;
