@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_pass_kernel(BinArgs a, in
     run += t;
   }
   const long long before_tile =
-      tile_exclusive_prefix(status + tid, tile, run, a.err, kRadixBins, a.wait_ns);
+      tile_exclusive_prefix_batched(status + tid, tile, run, a.err, kRadixBins, a.wait_ns);
   s_base[tid] = digit_base + (int)before_tile;
   __syncthreads();
 #pragma unroll

@@ -380,6 +380,14 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
   s_chunk[tid] = ex;
   const long long prefix = a.tile_prefix[blockIdx.x];
   const bool sorted = *a.unsorted == 0;
+  // grouped input: the cell ids of my positions, loaded while the bulk
+  // copies are in flight (ungrouped input reads them through the permutation)
+  int32_t cid[kEmitChunk];
+#pragma unroll
+  for (int j = 0; j < kEmitChunk; ++j) {
+    const int off = j * kEmitThreads + tid;
+    cid[j] = (sorted && off < cnt) ? a.cells[t0 + off] : 0;
+  }
   const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0, kWaitNs));
   if (late) {
     // never leave with copies in flight into this CTA's shared memory
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
     }
     if (a.out_index && (!EC || h == kHeadSingle)) a.out_index[orig] = (int32_t)slot;
     if (!h) continue;
-    const int32_t cell_id = a.cells[sorted ? t0 + off : (int64_t)orig];
+    const int32_t cell_id = sorted ? cid[j] : a.cells[orig];
     a.out_cell[slot] = cell_id;
     if (EC && h != kHeadSingle) a.out_cell[slot + 1] = cell_id;
     if (h == kHeadSingle) {

@@ -70,6 +70,67 @@ __device__ inline long long tile_exclusive_prefix(unsigned long long *status, in
   return prefix;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// As tile_exclusive_prefix, for a caller that reads nothing else its
+// predecessors wrote (only their status words): the walk loads the words of
+// kLookAhead predecessors at once (relaxed loads, so they are in flight
+// together) and sums them in order up to the first inclusive prefix, so a
+// long walk costs about 1/kLookAhead of the round trips.
+constexpr int kLookAhead = 8;
+
+__device__ inline long long tile_exclusive_prefix_batched(unsigned long long *status, int tile,
+                                                          long long aggregate, unsigned *err,
+                                                          int stride, unsigned long long wait_ns) {
+  if (tile == 0) {
+    st_release_u64(&status[0], kFlagInc | (unsigned long long)aggregate);
+    return 0;
+  }
+  st_release_u64(&status[(size_t)tile * stride], kFlagAgg | (unsigned long long)aggregate);
+  long long prefix = 0;
+  int t = tile - 1;  // newest predecessor not yet summed
+  unsigned long long t0 = 0;
+  while (t >= 0) {
+    unsigned long long sv[kLookAhead];
+#pragma unroll
+    for (int k = 0; k < kLookAhead; ++k)
+      sv[k] = t - k >= 0 ? ld_relaxed_u64(&status[(size_t)(t - k) * stride]) : kFlagInc;
+    int used = 0;
+    bool done = false, stalled = false;
+#pragma unroll
+    for (int k = 0; k < kLookAhead; ++k) {
+      if (done || stalled) continue;
+      const unsigned long long f = sv[k] >> 62;
+      if (f == 0) {
+        stalled = true;
+        continue;
+      }
+      prefix += (long long)(sv[k] & kValMask);
+      ++used;
+      if (f == 2) done = true;
+    }
+    if (done) break;
+    t -= used;
+    if (stalled) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > wait_ns) {
+        atomicOr(err, kErrTimeout);
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  st_release_u64(&status[(size_t)tile * stride],
+                 kFlagInc | (unsigned long long)(prefix + aggregate));
+  return prefix;
+}
+
 // Warp-wide version: called by all 32 lanes of one warp; examines 32
 // predecessors per step.  Returns the exclusive prefix of `tile` in every lane.
 // `publish` = false withholds this tile's status words (used only by the

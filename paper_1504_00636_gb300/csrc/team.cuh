@@ -976,6 +976,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     if (wt == 0 && passed) atomicAdd(&P.stats[kStCellsPass], passed);
   }
 }
+#undef PMA_SORTED_COPY
 
 // ----------------------------------------------------------------- launch
 
