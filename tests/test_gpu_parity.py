@@ -135,6 +135,34 @@ def test_ungrouped_input_sorts_stably(make, precision):
         compare(x, gx, _oracle(x))
 
 
+def _with_big_cells():
+    """A shower-shaped set in which two cells hold 9000 and 8000 particles:
+    above every large tile (7551 in float32 and 4223 in FP64 for D = 5), so
+    they are cut in global memory first and their pieces read the inputs
+    through the permutation, while the other cells read the sorted copy."""
+    p = synth.shower(grid=(24, 24), cap=3000)
+    cell = p.cell.copy()
+    cell[:9000] = 5
+    cell[9000:17000] = 7
+    return dataclasses.replace(p, name="shower_big_cells", cell=cell)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ungrouped_input_with_big_cells(precision):
+    x = _with_big_cells().shuffled(8)
+    if precision == "mixed":
+        x = x.astype(np.float32)
+    y, order = _grouped(x)
+    gx, gy = run_gpu(x, precision), run_gpu(y, precision)
+    assert gx["stats"]["sorted_input"] == 0 and gx["stats"]["big_cells"] == 2
+    for key in ("cell", "pos", "mom", "w"):
+        np.testing.assert_array_equal(gx[key], gy[key])
+    np.testing.assert_array_equal(gx["index"][order], gy["index"])
+    if precision == "fp64":
+        compare(x, gx, _oracle(x))
+        conservation(x, gx)
+
+
 def test_ungrouped_input_many_cells():
     # 2^18 + 3 cells need three 7-bit radix passes; most cells hold 0-3
     # particles; a few ids repeat far apart in the input
