@@ -180,6 +180,98 @@ __device__ __forceinline__ double kinetic(double w, double p2) {
   return w * p2 / (sqrt(1.0 + p2) + 1.0);
 }
 
+// ---- sums over the members of a merged set
+//
+// W = sum w and S1_l = sum w q_l over the members r = first, first + stride,
+// ... < end (in this tile's shared memory below t0 + cnt, else in global
+// memory), in FP64, where a product of two floats is exact.  The FP64 pipe of
+// this GPU is slow, so the plain float build forms each product exactly as
+// two floats (Ogita, Rump & Oishi's TwoProduct, with an FMA) and adds them
+// to a two-float accumulator whose leading part is updated by Knuth's
+// error-free TwoSum; every kFold members the accumulator is added to the FP64
+// sum.  The result differs from the exact sum by at most about
+// kFold^2 2^-48 (below 2.5e-13) of sum |w q| per fold.  The other builds
+// (FP64 storage, energy accounting) add in FP64 directly.
+constexpr int kFold = 8;
+
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void f2_add(F2 &a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float bp = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, err);
+}
+
+__device__ __forceinline__ void f2_add_prod(F2 &a, float w, float q) {
+  const float p = __fmul_rn(w, q);
+  const float e = __fmaf_rn(w, q, -p);  // w q = p + e exactly
+  f2_add(a, p);
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+__device__ __forceinline__ void f2_fold(double &d, F2 &a) {
+  d += to_f64<float>(a.hi);
+  d += to_f64<float>(a.lo);
+  a.hi = 0.f;
+  a.lo = 0.f;
+}
+
+template <typename T, bool EN, int DT>
+__device__ __forceinline__ void set_sums(const EmitArgs &a, const T *s_col, int64_t t0, int cnt,
+                                         int64_t first, int64_t end, int stride, double &W,
+                                         double *S1, double &ein) {
+  const int D = DT ? DT : a.dx + a.dp;
+  auto val = [&](int l, int64_t r) -> T {
+    return r < t0 + cnt ? s_col[l * kEmitTile + (int)(r - t0)]
+                        : static_cast<const T *>(a.fin[l])[r];
+  };
+  W = 0.0;
+#pragma unroll
+  for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
+  if constexpr (sizeof(T) == 4 && !EN) {
+    F2 fw{0.f, 0.f}, fs[kMaxD];
+#pragma unroll
+    for (int l = 0; l < kMaxD; ++l) fs[l] = F2{0.f, 0.f};
+    int k = 0;
+    for (int64_t r = first; r < end; r += stride) {
+      const float w = val(D, r);
+      f2_add(fw, w);
+#pragma unroll
+      for (int l = 0; l < kMaxD; ++l)
+        if (l < D) f2_add_prod(fs[l], w, val(l, r));
+      if (++k == kFold) {
+        k = 0;
+        f2_fold(W, fw);
+#pragma unroll
+        for (int l = 0; l < kMaxD; ++l)
+          if (l < D) f2_fold(S1[l], fs[l]);
+      }
+    }
+    f2_fold(W, fw);
+#pragma unroll
+    for (int l = 0; l < kMaxD; ++l)
+      if (l < D) f2_fold(S1[l], fs[l]);
+  } else {
+    for (int64_t r = first; r < end; r += stride) {
+      const double w = to_f64<T>(val(D, r));
+      W += w;
+      double p2 = 0.0;
+#pragma unroll
+      for (int l = 0; l < kMaxD; ++l)
+        if (l < D) {
+          const double q = to_f64<T>(val(l, r));
+          S1[l] = fma(w, q, S1[l]);
+          if (l >= a.dx) p2 = fma(q, q, p2);
+        }
+      if (EN) ein += kinetic(w, p2);
+    }
+  }
+}
+
 // EC: one final set of m >= 2 members at positions [p, e) of the staged
 // arrays (in this tile's shared memory below t0 + cnt, else in global
 // memory), first output slot `slot`.  m = 2: both members as they are.
@@ -331,16 +423,20 @@ __device__ void energy_set(const EmitArgs &a, const T *s_col, const int32_t *s_p
 // CTA meanwhile reads the head bytes and scans them into output slots.  The
 // positions are then handled in consecutive order across the threads, so the
 // output stores of runs of one-particle sets are coalesced.
-// CTAs per SM the plain builds are held to (float: at most 42 registers,
-// shared memory allows 7; FP64: at most 64, shared memory allows 4); the
-// energy-conserving and energy-accounting builds take the registers they need
-template <typename T, bool EC, bool EN>
+// CTAs per SM the plain builds are held to (float: 5 for D <= 4, 4 for
+// D = 5, 3 for D = 6, what their two-float sums need without spills; FP64: 4,
+// what its shared memory allows); the energy-conserving and energy-accounting
+// builds take the registers they need
+template <typename T, bool EC, bool EN, int DT>
 constexpr int emit_min_blocks() {
-  return (EC || EN) ? 1 : (sizeof(T) == 4 ? 6 : 4);
+  return (EC || EN) ? 1 : (sizeof(T) == 4 ? (DT <= 4 ? 5 : (DT == 5 ? 4 : 3)) : 4);
 }
 
-template <typename T, bool EC, bool EN>
-__global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
+// DT: the coordinate count D = dx + dp fixed at compile time (the plain
+// float builds, whose two-float sums need registers per axis), or 0 (read
+// from the arguments)
+template <typename T, bool EC, bool EN, int DT>
+__global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN, DT>()))
     emit_kernel(EmitArgs a) {
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ __align__(8) uint64_t s_bar;
@@ -352,7 +448,7 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
   __shared__ int2 s_merged[kEmitTile / 2 + 1];  // (offset in tile, output slot)
   if (timed_out(a.err)) return;
   const int tid = threadIdx.x;
-  const int D = a.dx + a.dp;
+  const int D = DT ? DT : a.dx + a.dp;
   const int64_t t0 = (int64_t)blockIdx.x * kEmitTile;
   const int cnt = (int)(a.n - t0 < (int64_t)kEmitTile ? a.n - t0 : (int64_t)kEmitTile);
   T *s_col = reinterpret_cast<T *>(s_dyn);  // column l at s_col[l * kEmitTile]
@@ -492,39 +588,8 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
       energy_set<T>(a, s_col, s_perm, t0, cnt, t0 + off, e, slot_m, ein, eout);
       continue;
     }
-    double W = 0.0, S1[kMaxD];
-#pragma unroll
-    for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
-    if (e <= t0 + cnt) {
-      // the whole set lies in this tile
-      for (int r = off; r < (int)(e - t0); ++r) {
-        const double w = to_f64<T>(s_col[D * kEmitTile + r]);
-        W += w;
-        double p2 = 0.0;
-#pragma unroll
-        for (int l = 0; l < kMaxD; ++l)
-          if (l < D) {
-            const double q = to_f64<T>(s_col[l * kEmitTile + r]);
-            S1[l] = fma(w, q, S1[l]);
-            if (l >= a.dx) p2 = fma(q, q, p2);
-          }
-        if (EN) ein += kinetic(w, p2);
-      }
-    } else {
-      for (int64_t r = t0 + off; r < e; ++r) {
-        const double w = to_f64<T>(static_cast<const T *>(a.fin[D])[r]);
-        W += w;
-        double p2 = 0.0;
-#pragma unroll
-        for (int l = 0; l < kMaxD; ++l)
-          if (l < D) {
-            const double q = to_f64<T>(static_cast<const T *>(a.fin[l])[r]);
-            S1[l] = fma(w, q, S1[l]);
-            if (l >= a.dx) p2 = fma(q, q, p2);
-          }
-        if (EN) ein += kinetic(w, p2);
-      }
-    }
+    double W, S1[kMaxD];
+    set_sums<T, EN, DT>(a, s_col, t0, cnt, t0 + off, e, 1, W, S1, ein);
     const double inv = 1.0 / W;
     a.out_w[slot_m] = W;
     double P2 = 0.0;
@@ -571,26 +636,8 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
         internal = true;
         e = a.n;
       }
-      double W = 0.0, S1[kMaxD];
-#pragma unroll
-      for (int l = 0; l < kMaxD; ++l) S1[l] = 0.0;
-      for (int64_t r = t0 + off + lane; r < e; r += 32) {
-        const bool here = r < t0 + cnt;
-        const int rl = (int)(r - t0);
-        const double w = to_f64<T>(here ? s_col[D * kEmitTile + rl]
-                                        : static_cast<const T *>(a.fin[D])[r]);
-        W += w;
-        double p2 = 0.0;
-#pragma unroll
-        for (int l = 0; l < kMaxD; ++l)
-          if (l < D) {
-            const double q = to_f64<T>(here ? s_col[l * kEmitTile + rl]
-                                            : static_cast<const T *>(a.fin[l])[r]);
-            S1[l] = fma(w, q, S1[l]);
-            if (l >= a.dx) p2 = fma(q, q, p2);
-          }
-        if (EN) ein += kinetic(w, p2);
-      }
+      double W, S1[kMaxD];
+      set_sums<T, EN, DT>(a, s_col, t0, cnt, t0 + off + lane, e, 32, W, S1, ein);
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
         W += __shfl_xor_sync(full, W, o);
@@ -657,7 +704,7 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN>()))
   if (internal) atomicOr(a.err, kErrInternal);
 }
 
-template <typename T, bool EC, bool EN>
+template <typename T, bool EC, bool EN, int DT = 0>
 static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   const size_t smem = emit_smem_bytes(a.dx + a.dp, sizeof(T) == 4);
   // raise the dynamic shared-memory limit once per device
@@ -666,12 +713,12 @@ static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || (int)smem > limit_set[dev]) {
-    e = cudaFuncSetAttribute(emit_kernel<T, EC, EN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(emit_kernel<T, EC, EN, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
   }
-  emit_kernel<T, EC, EN><<<a.tiles, kEmitThreads, smem, st>>>(a);
+  emit_kernel<T, EC, EN, DT><<<a.tiles, kEmitThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -692,8 +739,14 @@ cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
   }
   if (en) return a.mixed ? launch_emit_t<float, false, true>(a, st)
                          : launch_emit_t<double, false, true>(a, st);
-  return a.mixed ? launch_emit_t<float, false, false>(a, st)
-                 : launch_emit_t<double, false, false>(a, st);
+  if (!a.mixed) return launch_emit_t<double, false, false>(a, st);
+  switch (a.dx + a.dp) {
+    case 2: return launch_emit_t<float, false, false, 2>(a, st);
+    case 3: return launch_emit_t<float, false, false, 3>(a, st);
+    case 4: return launch_emit_t<float, false, false, 4>(a, st);
+    case 5: return launch_emit_t<float, false, false, 5>(a, st);
+    default: return launch_emit_t<float, false, false, 6>(a, st);
+  }
 }
 
 }  // namespace pma
