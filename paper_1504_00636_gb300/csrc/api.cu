@@ -114,6 +114,10 @@ struct pma_handle {
   cudaEvent_t *cur_ev = nullptr;
   std::string last_error;
   pma_stats stats{};
+  // the counts of the handle's last call that completed without error: a
+  // work source that was empty then gets a small grid now (see enqueue)
+  bool have_prev = false;
+  pma_stats prev{};
 };
 
 namespace {
@@ -273,6 +277,7 @@ void apply_classes(pma_handle *h, const Classes &c) {
   h->cap = c.cap;
   h->class_base = c.base;
   h->widen_groups = c.widen;
+  h->have_prev = false;  // the last call's counts per class no longer apply
   h->warp_grid =
       h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap_w) + 1024)));
   // (about 24 one-warp CTAs per SM are resident at the kernel's register use)
@@ -569,21 +574,31 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   P.block_list = h->block_list;
   P.block_count = &h->ctl->block_count;
 
-  e = launch_gather(P, n, h->mixed, h->sms, st);
+  // Launch sizes.  Every kernel below takes its work by ticket or in a
+  // grid-stride loop, so any grid of at least one CTA gives the same result.
+  // A work source that was empty in the handle's last completed call (for
+  // a PIC code, the previous time step) gets a quarter of a CTA per SM: a
+  // launch that finds nothing to do then costs less, and one that does find
+  // work still does it, only with fewer CTAs.
+  auto grid_for = [&](bool was_empty, int grid) {
+    return (h->have_prev && was_empty) ? std::min(grid, std::max(1, h->sms / 4)) : grid;
+  };
+  const pma_stats &pv = h->prev;
+  e = launch_gather(P, n, h->mixed, grid_for(pv.sorted_input != 0, h->sms * 8), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "gather launch");
   mark(h, 1, st);  // Step 1 done: binned (and, for ungrouped input, copied in sorted order)
-  e = launch_big(P, h->mixed, h->sms * 4, st);
+  e = launch_big(P, h->mixed, grid_for(pv.big_cells == 0, h->sms * 4), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "big-cell launch");
   mark(h, 2, st);
-  e = launch_team(P, h->mixed, 3, 1, h->cap_t, h->tiny_grid, st);
+  e = launch_team(P, h->mixed, 3, 1, h->cap_t, grid_for(pv.cells_tiny == 0, h->tiny_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (tiny cells)");
-  e = launch_team(P, h->mixed, 0, 4, h->cap_w, h->warp_grid, st);
+  e = launch_team(P, h->mixed, 0, 4, h->cap_w, grid_for(pv.cells_small == 0, h->warp_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (small cells)");
   mark(h, 3, st);
-  e = launch_team(P, h->mixed, 1, 8, h->cap, h->unit_grid, st);
+  e = launch_team(P, h->mixed, 1, 8, h->cap, grid_for(pv.cells_large == 0, h->unit_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (large cells)");
   mark(h, 4, st);
-  e = launch_team(P, h->mixed, 2, 8, h->cap, h->unit_grid, st);
+  e = launch_team(P, h->mixed, 2, 8, h->cap, grid_for(pv.big_cells == 0, h->unit_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (pieces)");
   mark(h, 5, st);
 
@@ -652,6 +667,10 @@ int pma_sync(pma_handle *h) {
   int64_t n_in = h->stats.n_in;
   int rc = status_from_ctl(h);
   h->stats.n_in = n_in;
+  if (rc == PMA_OK) {
+    h->prev = h->stats;
+    h->have_prev = true;
+  }
   return rc;
 }
 

@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(256) gather_kernel(Problem P, int64_t n) {
   }
 }
 
-cudaError_t launch_gather(const Problem &P, int64_t n, int mixed, int sms, cudaStream_t st) {
+cudaError_t launch_gather(const Problem &P, int64_t n, int mixed, int grid_max, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, grid_max));
   if (mixed)
     gather_kernel<float><<<grid, 256, 0, st>>>(P, n);
   else

@@ -67,7 +67,8 @@ constexpr int kRadixMaxPasses = 4;
 constexpr int kRadixBins = 256;
 cudaError_t launch_binning(const BinArgs &a, int sms, cudaStream_t st);
 // ungrouped input: the particles in sorted order into the staging columns
-cudaError_t launch_gather(const Problem &P, int64_t n, int mixed, int sms, cudaStream_t st);
+// (grid-stride: any grid of at least one CTA is correct)
+cudaError_t launch_gather(const Problem &P, int64_t n, int mixed, int grid_max, cudaStream_t st);
 int scan_tiles_for(int64_t n);
 int radix_tiles_for(int64_t n);
 // passes and bit split of the cell-id keys (values 0..n_cells, n_cells marks

@@ -163,6 +163,35 @@ def test_ungrouped_input_with_big_cells(precision):
         conservation(x, gx)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_work_after_an_empty_call_gets_done(precision):
+    # a handle sizes the launches of work sources that were empty in its last
+    # call small; when such a source has work in the next call (here: tiny
+    # cells, big cells and ungrouped input after a call with none of them)
+    # the result must still equal a fresh handle's
+    first = synth.two_stream(cells=64)
+    second = _with_big_cells().shuffled(9)
+    if precision == "mixed":
+        first, second = first.astype(np.float32), second.astype(np.float32)
+    # one handle sized for both (same cell count and dimensions for both runs)
+    n_cells = max(first.n_cells, second.n_cells)
+    a = dataclasses.replace(first, n_cells=n_cells, dx=second.dx,
+                            pos=np.concatenate([first.pos, first.pos[:1]])
+                            if first.dx < second.dx else first.pos,
+                            cell_size=second.cell_size)
+    m = binding.Merger(second.dx, second.dp, n_cells, max(a.n, second.n), second.cell_size, 0,
+                       precision)
+    ga = run_gpu(a, precision, merger=m)
+    assert ga["stats"]["cells_tiny"] == 0 and ga["stats"]["big_cells"] == 0
+    assert ga["stats"]["sorted_input"] == 1
+    g = run_gpu(second, precision, merger=m)
+    fresh = run_gpu(second, precision)
+    assert g["stats"]["big_cells"] == 2 and g["stats"]["cells_tiny"] > 0
+    for key in ("cell", "pos", "mom", "w", "index"):
+        np.testing.assert_array_equal(g[key], fresh[key])
+    m.close()
+
+
 def test_ungrouped_input_many_cells():
     # 2^18 + 3 cells need three 7-bit radix passes; most cells hold 0-3
     # particles; a few ids repeat far apart in the input
