@@ -229,6 +229,24 @@ int pma_merge_host(pma_handle *h, int64_t n, const int32_t *cells,
 int pma_set_wait_limit(pma_handle *h, int64_t wait_ns);
 
 /*
+ * Bounds-checked build (no counterpart in the paper; it stands in for a
+ * memory sanitizer).  A library compiled with -DPMA_CHECKED checks the
+ * indices the partition and output kernels use: subset records and tile
+ * indices against the shared-memory tile, cut destinations against their
+ * subset, final positions and output slots against n, and the cuts of big
+ * cells against their cell.  The first index out of range in a call is
+ * recorded, its access is skipped, and the call returns PMA_ERR_INTERNAL.
+ * pma_checked_build returns 1 for such a library and 0 otherwise.
+ * pma_check_first gives the record of the handle's last synchronised call:
+ * 0 when every check passed, else (site << 48) | index, the sites numbered
+ * 1 subset record, 2 tile index, 3 cut destination, 4 pair record, 5 final
+ * position, 6 output slot, 7 big-cell position.  The normal build compiles
+ * no checks and always reports 0.
+ */
+int pma_checked_build(void);
+int pma_check_first(const pma_handle *h, uint64_t *site_index);
+
+/*
  * Failure-detection test hook (not for production use; no counterpart in
  * the paper): while `tile` >= 0, every call's Step 1 prefix scan withholds
  * the status word of that scan tile (a tile covers 2048 cells), so that the

@@ -33,17 +33,22 @@ def _flags(extra=()):
                    "-I" + INCLUDE, "-I" + CSRC] + list(extra)
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = None) -> bool:
+    lib = lib or LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "pma.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA source and link ``libpma.so``; returns its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, extra=(), lib: str = None,
+          objdir: str = None) -> str:
+    """Compile every CUDA source and link ``libpma.so`` (or `lib`); returns
+    its path."""
+    LIB = lib or globals()["LIB"]
+    BUILD = objdir or globals()["BUILD"]
+    if not force and not _stale(LIB):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -72,6 +77,16 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
     return LIB
+
+
+CHECKED_LIB = os.path.join(HERE, "libpma_checked.so")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked build (-DPMA_CHECKED) as ``libpma_checked.so``,
+    objects in their own folder; load it with PMA_LIBRARY."""
+    return build(force=force, extra=("-DPMA_CHECKED",), lib=CHECKED_LIB,
+                 objdir=os.path.join(HERE, "_build_checked"))
 
 
 if __name__ == "__main__":

@@ -42,7 +42,7 @@ SYMBOLS = ("pma_create", "pma_merge", "pma_merge_host", "pma_sync", "pma_get_sta
            "pma_error_string", "pma_last_error", "pma_set_wait_limit",
            "pma_test_withhold_status", "pma_test_status_of_bits", "pma_probe_fma",
            "pma_get_classes", "pma_set_classes", "pma_tune", "pma_tune_cache_lookup",
-           "pma_tune_cache_store")
+           "pma_tune_cache_store", "pma_checked_build", "pma_check_first")
 PMA_NOALLOC_MAX_N = 65536
 PMA_NOALLOC_MAX_CELLS = 65536
 PMA_N_STAGES = 7
@@ -87,12 +87,14 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load ``libpma.so`` (building it with nvcc when absent or stale)."""
+    """Load ``libpma.so`` (building it with nvcc when absent or stale).  The
+    environment variable PMA_LIBRARY names another build of the library to
+    load instead, such as the bounds-checked one (``_build.build_checked``)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if build_if_missing:
+            path = os.environ.get("PMA_LIBRARY") or _build.LIB
+            if build_if_missing and not os.environ.get("PMA_LIBRARY"):
                 path = _build.build()
             if not os.path.exists(path):
                 raise RuntimeError("libpma.so not found at %s; run __graft_entry__.build()" % path)
@@ -118,6 +120,10 @@ def load(build_if_missing: bool = True):
             lib.pma_merge_noalloc.restype = ctypes.c_int
             lib.pma_set_wait_limit.argtypes = [P, ctypes.c_int64]
             lib.pma_set_wait_limit.restype = ctypes.c_int
+            lib.pma_checked_build.argtypes = []
+            lib.pma_checked_build.restype = ctypes.c_int
+            lib.pma_check_first.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+            lib.pma_check_first.restype = ctypes.c_int
             lib.pma_test_withhold_status.argtypes = [P, ctypes.c_int]
             lib.pma_test_withhold_status.restype = ctypes.c_int
             caps = ctypes.POINTER(ctypes.c_int32)
@@ -220,6 +226,19 @@ def pma_sync(handle) -> None:
 
 def pma_set_wait_limit(handle, wait_ns: int) -> None:
     _check(load().pma_set_wait_limit(handle, int(wait_ns)), handle)
+
+
+def pma_checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return load().pma_checked_build() == 1
+
+
+def pma_check_first(handle):
+    """(site, index) of the first failed bounds check of the handle's last
+    synchronised call, or None (always None in the normal build)."""
+    v = ctypes.c_uint64(0)
+    _check(load().pma_check_first(handle, ctypes.byref(v)), handle)
+    return None if v.value == 0 else (v.value >> 48, v.value & ((1 << 48) - 1))
 
 
 def pma_test_withhold_status(handle, tile: int) -> None:

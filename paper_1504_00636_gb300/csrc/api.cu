@@ -50,6 +50,7 @@ struct Ctl {
   int64_t count;
   unsigned long long stats[kStCount];
   double energy[2];  // kinetic energy in and out (PMA_FLAG_ENERGY_STATS)
+  unsigned long long check;  // first failed bounds check (checked build), site << 48 | index
 };
 
 constexpr int kRing = 64;  // timed calls kept for pma_get_timing
@@ -117,6 +118,7 @@ struct pma_handle {
   // the counts of the handle's last call that completed without error: a
   // work source that was empty then gets a small grid now (see enqueue)
   bool have_prev = false;
+  unsigned long long check_first = 0;  // the last synced call's first failed bounds check
   pma_stats prev{};
 };
 
@@ -182,6 +184,7 @@ int status_of_bits(unsigned err) {
 int status_from_ctl(pma_handle *h) {
   const Ctl &c = *h->ctl_host;
   pma_stats &s = h->stats;
+  h->check_first = c.check;
   s.n_out = c.count;
   s.cells_merged = (int64_t)c.stats[kStCellsMerged];
   s.cells_passthrough = (int64_t)c.stats[kStCellsPass];
@@ -520,6 +523,8 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   if (e != cudaSuccess) return cuda_fail(h, e, "binning launch");
 
   Problem P{};
+  P.n = n;
+  P.check = &h->ctl->check;
   P.n_cells = (int32_t)C;
   P.dx = h->cfg.dx;
   P.D = h->D;
@@ -604,6 +609,7 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
 
   EmitArgs m{};
   m.n = n;
+  m.check = &h->ctl->check;
   m.dx = h->cfg.dx;
   m.dp = h->cfg.dp;
   m.mixed = h->mixed;
@@ -702,6 +708,14 @@ int pma_get_timing(const pma_handle *h, float *ms, int n) {
     }
     ms[i] = (float)(sum / calls);
   }
+  return PMA_OK;
+}
+
+int pma_checked_build(void) { return kChecked ? 1 : 0; }
+
+int pma_check_first(const pma_handle *h, uint64_t *site_index) {
+  if (!h || !site_index) return PMA_ERR_INVALID_ARG;
+  *site_index = h->check_first;
   return PMA_OK;
 }
 

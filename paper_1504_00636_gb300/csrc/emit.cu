@@ -516,6 +516,9 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN, DT>(
       internal = true;
       continue;
     }
+    if (!check_index(a.check, a.err, slot >= 0 && slot + ((EC && h > 1) ? 1 : 0) < a.n,
+                     kChkEmitSlot, slot))
+      continue;
     if (a.out_index && (!EC || h == kHeadSingle)) a.out_index[orig] = (int32_t)slot;
     if (!h) continue;
     const int32_t cell_id = sorted ? cid[j] : a.cells[orig];
@@ -572,6 +575,7 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN, DT>(
     const long long slot_m = s_merged[k].y;
     const int h = s_head[off];
     if (!EC && h >= kWarpSet) continue;  // summed by a warp below
+    if (!check_index(a.check, a.err, slot_m + (EC ? 1 : 0) < a.n, kChkEmitSlot, slot_m)) continue;
     // members: the head's count, or (255) every position up to the next head
     int64_t e = t0 + off + h;
     if (h == kHeadLong) {
@@ -617,6 +621,7 @@ __global__ void __launch_bounds__(kEmitThreads, (emit_min_blocks<T, EC, EN, DT>(
       const int h = s_head[off];
       if (h < kWarpSet) continue;  // warp-uniform
       const long long slot_m = s_merged[k].y;
+      if (!check_index(a.check, a.err, slot_m < a.n, kChkEmitSlot, slot_m)) continue;  // warp-uniform
       int64_t e = t0 + off + h;
       if (h == kHeadLong) {
         // the next head (or the end), 32 head bytes per step

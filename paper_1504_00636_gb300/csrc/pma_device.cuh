@@ -26,6 +26,38 @@ constexpr unsigned kErrInput = 1u;
 constexpr unsigned kErrInternal = 2u;
 constexpr unsigned kErrTimeout = 4u;
 
+// Bounds-checked build (compiled with -DPMA_CHECKED, in place of a memory
+// sanitizer): an index that a check finds out of range records the site and
+// the index of the first such failure of the call in *check, sets
+// kErrInternal, and the access it guards is skipped.  In the normal build
+// every check is the constant true and compiles to nothing.
+enum CheckSite : unsigned {
+  kChkRecord = 1,   // a subset record outside the tile
+  kChkTileIndex,    // a tile index read from an index buffer
+  kChkCutDest,      // a cut's destination outside its subset
+  kChkPair,         // a two-particle record outside the tile
+  kChkStage,        // a final position outside the workspace
+  kChkEmitSlot,     // an output slot outside the output arrays
+  kChkCluster       // a position outside the cell being cut in global memory
+};
+
+#ifdef PMA_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool check_index(unsigned long long *check, unsigned *err, bool ok,
+                                            unsigned site, long long index) {
+  if (kChecked && !ok) {
+    if (check)
+      atomicCAS(check, 0ull,
+                ((unsigned long long)site << 48) | ((unsigned long long)index & 0xffffffffffffull));
+    atomicOr(err, kErrInternal);
+  }
+  return kChecked ? ok : true;
+}
+
 // counters kept on the device (indices into Problem::stats)
 enum Stat {
   kStCellsMerged = 0,
@@ -59,6 +91,8 @@ constexpr int kVarNormalized = 2;  // Step 4 on Delta_l / T_l
 constexpr int kVarPNorm = 4;       // Eq. cv_p with |P| of the mean momentum vector
 
 struct Problem {
+  int64_t n;              // particles of the call
+  unsigned long long *check;  // first failed bounds check (checked build)
   int32_t n_cells;
   int32_t dx;
   int32_t D;

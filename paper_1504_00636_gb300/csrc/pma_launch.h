@@ -78,6 +78,7 @@ void radix_plan(BinArgs &a);
 // emit.cu
 struct EmitArgs {
   int64_t n;
+  unsigned long long *check;  // first failed bounds check (checked build)
   int32_t dx, dp, mixed;
   int32_t ec;  // energy-conserving replacement (PMA_FLAG_CONSERVE_ENERGY)
   const uint8_t *head;

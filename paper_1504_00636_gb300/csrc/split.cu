@@ -527,7 +527,9 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
             if (valid) {
               const int64_t dst = lft ? (b + cntL + wL + __popc(bl & lt))
                                       : (e - 1 - cntR - wR - __popc(br & lt));
-              P.perm_tmp[dst] = src;
+              if (check_index(P.check, P.err, dst >= b && dst < e && (unsigned)src < (unsigned)P.n,
+                              kChkCluster, dst))
+                P.perm_tmp[dst] = src;
             }
             cntL += tL;
             cntR += tR;

@@ -352,7 +352,9 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
   const unsigned full = 0xffffffffu;
   const int G = 1 << lg;
   const int gid = lane >> lg, gl = lane & (G - 1);
-  const bool act = gid < kw;
+  const bool act = gid < kw && check_index(P.check, P.err,
+                                           rec_len(rec) >= 2 && rec_begin(rec) + rec_len(rec) <= S.cap,
+                                           kChkRecord, rec_begin(rec));
   const int b = rec_begin(rec), m = act ? rec_len(rec) : 0, par = rec_par(rec);
   const uint16_t *ix = S.idx(par);
 
@@ -375,6 +377,7 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
 #pragma unroll 4
     for (int i = gl; i < m; i += G) {
       const int j = ix[b + i];
+      if (!check_index(P.check, P.err, j < S.cap, kChkTileIndex, j)) continue;
       T q[D];
 #pragma unroll
       for (int l = 0; l < D; ++l) q[l] = S.col(l)[j];
@@ -402,10 +405,12 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
 #pragma unroll 4
       for (int i = 0; i < m; ++i) {
         const int j = ix[b + i];
+        if (!check_index(P.check, P.err, j < S.cap, kChkTileIndex, j)) continue;
         const T q = qk[j];
         nr |= Decider<T, D, VAR>::near(q, cut);
         const int dst = Decider<T, D, VAR>::left(q, cut) ? (b + cntL++) : (b + m - 1 - cntR++);
-        S.idx(np)[dst] = (uint16_t)j;
+        if (check_index(P.check, P.err, dst >= b && dst < b + m, kChkCutDest, dst))
+          S.idx(np)[dst] = (uint16_t)j;
       }
   } else {
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (gid * G));
@@ -413,8 +418,10 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
     const int mmax = __reduce_max_sync(full, split ? (unsigned)m : 0u);
     for (int base = 0; base < mmax; base += G) {
       const int i = base + gl;
-      const bool valid = split && i < m;
-      const int j = valid ? ix[b + i] : 0;
+      int j = (split && i < m) ? ix[b + i] : 0;
+      const bool valid =
+          split && i < m && check_index(P.check, P.err, j < S.cap, kChkTileIndex, j);
+      if (!valid) j = 0;
       const T q = qk[j];
       const bool lft = valid && Decider<T, D, VAR>::left(q, cut);
       nr |= valid && Decider<T, D, VAR>::near(q, cut);
@@ -423,7 +430,8 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
       if (valid) {
         const int dst =
             lft ? (b + cntL + __popc(bl & lt)) : (b + m - 1 - cntR - __popc(br & lt));
-        S.idx(np)[dst] = (uint16_t)j;
+        if (check_index(P.check, P.err, dst >= b && dst < b + m, kChkCutDest, dst))
+          S.idx(np)[dst] = (uint16_t)j;
       }
       cntL += __popc(bl);
       cntR += __popc(br);
@@ -605,7 +613,8 @@ template <typename T, int D, bool VAR>
 __device__ unsigned pair_round(const Problem &P, const WarpTile<T, D> &S, const int32_t *perm,
                                int64_t gb, int lane, Counters &cnt, int kw, uint32_t rec) {
   constexpr bool kF = sizeof(T) == 4;
-  const bool act = lane < kw;
+  const bool act = lane < kw && check_index(P.check, P.err, rec_begin(rec) + 1 < S.cap,
+                                            kChkPair, rec_begin(rec));
   const int b = rec_begin(rec), par = rec_par(rec);
   bool redo = false;
   if (act) {
@@ -940,6 +949,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           P.head[gb + i] = 0;
           continue;
         }
+        if (!check_index(P.check, P.err, gb + i < P.n, kChkStage, gb + i)) continue;
         P.perm_final[gb + i] = orig_index(perm, gb, j);
         P.head[gb + i] = (uint8_t)S.idx(1)[i];
         stage<T, D>(P, S, gb + i, j);
