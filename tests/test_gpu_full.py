@@ -64,3 +64,32 @@ def test_shower_full_mixed():
 
 def test_hot_6d_full_mixed():
     _sampled_parity(synth.hot_6d(), "mixed")
+
+
+def test_two_stream_full_mixed_in_the_benchmarked_configuration():
+    # the bench times the two-stream workload with the classes pma_tune picks;
+    # at full size that run must give the default classes' result bit for bit
+    # (certified decisions), and agree with the oracle on sampled cells
+    import torch
+    from paper_1504_00636_gb300 import binding
+    p = synth.two_stream().astype(np.float32)
+    g_default = _sampled_parity(p, "mixed")
+    m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, "mixed")
+    dev = torch.device("cuda", 0)
+    cells = torch.from_numpy(p.cell).to(dev)
+    pos = [torch.from_numpy(np.ascontiguousarray(p.pos[a])).to(dev) for a in range(p.dx)]
+    mom = [torch.from_numpy(np.ascontiguousarray(p.mom[a])).to(dev) for a in range(p.dp)]
+    w = torch.from_numpy(np.ascontiguousarray(p.w)).to(dev)
+    caps = m.tune(cells, pos, mom, w, p.tol_x, p.tol_p)
+    g_tuned = run_gpu(p, "mixed", merger=m)
+    m.close()
+    flagged = (g_default["flags"] | g_tuned["flags"]) & binding.PMA_NEAR_ANY
+    if not flagged.any():
+        for key in ("cell", "pos", "mom", "w", "index"):
+            np.testing.assert_array_equal(g_tuned[key], g_default[key], err_msg=str(caps))
+    else:
+        from parity import local_index
+        li_d = local_index(g_default["index"], p.cell, g_default["cell"], p.n_cells)
+        li_t = local_index(g_tuned["index"], p.cell, g_tuned["cell"], p.n_cells)
+        keep = flagged[p.cell] == 0
+        np.testing.assert_array_equal(li_t[keep], li_d[keep], err_msg=str(caps))
