@@ -85,8 +85,8 @@ struct WarpTile {
   int *top;        // [kClasses] stack heights
   uint16_t *soff;  // [kClasses] first entry of each stack (class 1: the end
                    // of the region shared with class 0), [kClasses] capacities
-  int *ev;         // [kEvWords]: near-tie bits of the current unit, then the
-                   // CTA's counts of near-ties by kind and of FP64 rechecks
+  int *ev;         // [kEvWords]: the batch's unit table, the CTA's counts of
+                   // near-ties by kind and of FP64 rechecks
   const DecideConsts *dk;  // the FP64 decision's constants (for rechecks)
   void *wide;      // wide rounds: [kMaxTeam] partial moments, [kMaxTeam] counts
   int cap;
@@ -100,10 +100,23 @@ struct WarpTile {
   __device__ __forceinline__ int stk_cap(int c) const { return soff[kClasses + c]; }
 };
 
+// A tile holds a batch of up to kMaxBatch units (consecutive units of the
+// team's ticket chunk that fit together), cut in the same rounds, so that the
+// sets of several small cells fill one round's lanes.  Their sets stay
+// disjoint ranges of the tile, and each unit's final positions stay its own.
+constexpr int kMaxBatch = 8;
+
 // control words after the class stack heights: the unit ticket, then kEvWords
-// event words (unit near-tie bits; near-stop, near-argmax, near-cut and
-// recheck counts)
-constexpr int kEvWords = 5;
+// words: the batch's unit count, the CTA's near-stop, near-argmax, near-cut
+// and recheck counts, then per unit of the batch its near-tie bits, first
+// tile position, size, first sorted position and cell
+constexpr int kEvBatchN = 0;
+constexpr int kEvBits = 5;
+constexpr int kEvOff = kEvBits + kMaxBatch;
+constexpr int kEvN = kEvOff + kMaxBatch;
+constexpr int kEvGb = kEvN + kMaxBatch;
+constexpr int kEvCell = kEvGb + kMaxBatch;
+constexpr int kEvWords = kEvCell + kMaxBatch;
 
 template <typename T, int D>
 __host__ __device__ inline size_t warp_region_bytes(int cap) {
@@ -179,10 +192,14 @@ __device__ __forceinline__ void push_child(const Problem &P, const WarpTile<T, D
   cnt.leaves += push_set<T, D>(P.err, S, b, m, par);
 }
 
-// A rare event of one decision: near-tie bits (kNear*) and rechecks
-// (kRechecked), into the unit's bits and the CTA's counts.
-static __device__ __noinline__ void note_event_words(int *ev, unsigned bits) {
-  atomicOr(reinterpret_cast<unsigned *>(&ev[0]), bits);
+// A rare event of one decision on the set that starts at tile position b:
+// near-tie bits (kNear*) and rechecks (kRechecked), into the bits of the
+// batch unit that holds b and into the CTA's counts.
+static __device__ __noinline__ void note_event_words(int *ev, int b, unsigned bits) {
+  const int nb = ev[kEvBatchN];
+  int u = 0;
+  while (u + 1 < nb && b >= ev[kEvOff + u + 1]) ++u;
+  atomicOr(reinterpret_cast<unsigned *>(&ev[kEvBits + u]), bits);
   if (bits & kNearStop) atomicAdd(&ev[1], 1);
   if (bits & kNearArgmax) atomicAdd(&ev[2], 1);
   if (bits & kNearCut) atomicAdd(&ev[3], 1);
@@ -190,8 +207,8 @@ static __device__ __noinline__ void note_event_words(int *ev, unsigned bits) {
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void note_event(const WarpTile<T, D> &S, unsigned bits) {
-  note_event_words(S.ev, bits);
+__device__ __forceinline__ void note_event(const WarpTile<T, D> &S, int b, unsigned bits) {
+  note_event_words(S.ev, b, bits);
 }
 
 // Longest run of terms one lane adds in plain FP32 before the run is folded
@@ -297,7 +314,7 @@ __device__ __forceinline__ unsigned exact_set(WarpTile<T, D> S, unsigned *err, i
     nr = __any_sync(full, nr);
   }
   __syncwarp();
-  if (lane == 0) note_event<T, D>(S, kRechecked | cut.near | (nr ? kNearCut : 0u));
+  if (lane == 0) note_event<T, D>(S, b, kRechecked | cut.near | (nr ? kNearCut : 0u));
   const bool degenerate = !cut.leaf && (cntL == 0 || cntL == m);
   unsigned counts = 0u;
   if (cut.leaf || degenerate) {
@@ -391,7 +408,7 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
   if (act) cut = Decider<T, D, VAR>::run(P, M, s, m, run);
   // FP32 storage: a decision too close to call is taken again in FP64
   bool redo = kF && cut.unsure;
-  if (cut.near && gl == 0) note_event<T, D>(S, cut.near);
+  if (cut.near && gl == 0) note_event<T, D>(S, b, cut.near);
   const bool split = act && !cut.leaf && !redo;
   // Step 6: cut by group-masked ballot scan into the other index buffer;
   // nr: some particle in the cut's near band
@@ -443,7 +460,7 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
     if (kF)
       redo = true;  // an FP32 cut value too close to a particle: retake in FP64
     else if (gl == 0)
-      note_event<T, D>(S, kNearCut);
+      note_event<T, D>(S, b, kNearCut);
   }
   const bool degenerate = split && !redo && (cntL == 0 || cntR == 0);
   const bool final_set = act && !redo && (cut.leaf || degenerate);
@@ -524,7 +541,7 @@ __device__ bool wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
     cut = Decider<T, D, VAR>::run(P, Mt, s, m, run);
   }
   bool redo = kF && cut.unsure;
-  if (cut.near && wl == 0 && lane == 0) note_event<T, D>(S, cut.near);
+  if (cut.near && wl == 0 && lane == 0) note_event<T, D>(S, b, cut.near);
   const bool split = act && !cut.leaf && !redo;
   // Step 6: two passes over this warp's segment
   const int np = par ^ 1;
@@ -563,7 +580,7 @@ __device__ bool wide_round(const Problem &P, const WarpTile<T, D> &S, const int3
     if (kF)
       redo = true;
     else if (wl == 0 && lane == 0)
-      note_event<T, D>(S, kNearCut);
+      note_event<T, D>(S, b, kNearCut);
   }
   if (split && !redo) {
     uint16_t *ox = S.idx(np);
@@ -650,7 +667,7 @@ __device__ unsigned pair_round(const Problem &P, const WarpTile<T, D> &S, const 
     redo = kF && cut.unsure;
     if (!redo) {
       const unsigned ev = cut.near | (nr ? kNearCut : 0u);
-      if (ev) note_event<T, D>(S, ev);
+      if (ev) note_event<T, D>(S, b, ev);
       bool merged = cut.leaf != 0;
       int first = ja, second = jb;
       if (!merged) {
@@ -772,7 +789,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
       S.soff[tt] = (uint16_t)(tt == 0 ? 0 : o);
       S.soff[kClasses + tt] = (uint16_t)class_capacity(tt, cap, S.base);
     }
-    if (tt < kEvWords) S.ev[tt] = 0;
+    for (int i = tt; i < kEvWords; i += kThreads) S.ev[i] = 0;
   }
   const int32_t *perm = (U.mode == 2 || *P.unsorted != 0) ? P.perm : nullptr;
   // ungrouped input: the cells' particles were copied in sorted order into
@@ -780,7 +797,11 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
   // pieces of big cells still read the inputs through the permutation
   // (recomputed where needed rather than held in a register)
 #define PMA_SORTED_COPY (perm != nullptr && U.mode != 2)
-  const int chunk = (U.mode == 0 || U.mode == 3) ? kWarpChunk : 1;
+  // cells per ticket: kWarpChunk, or kMaxBatch when the class has many cells
+  // for the grid (more cells to pack into one tile); one piece or large cell
+  const int chunk = (U.mode == 0 || U.mode == 3)
+                        ? (count >= (int)gridDim.x * 32 ? kMaxBatch : kWarpChunk)
+                        : 1;
   Counters cnt{0u, 0u, 0u, 0ull};
   unsigned long long merged = 0, passed = 0;
 
@@ -795,89 +816,119 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
     __syncthreads();
     if (c0 >= count) break;
     const int c1 = min(c0 + chunk, count);
-    for (int t = c0; t < c1; ++t) {
-      int64_t gb;
-      int n, depth0, cell;
-      unit_at(P, U, t, gb, n, depth0, cell);
-      if (U.mode != 2 && (n <= P.n_min || n == 1)) {
-        // Sec. 3 "Input": cells with at most N_min particles are not merged
-        for (int i = tt; i < n; i += kThreads) {
-          const int src = orig_index(perm, gb, i);
-          P.perm_final[gb + i] = src;
-          P.head[gb + i] = kHeadSingle;
-          if (!PMA_SORTED_COPY) {  // (the sorted copy already sits there)
+    int t = c0;
+    while (t < c1) {
+      // the batch: the next units of the chunk that fit the tile together
+      // (pass-through cells on the way are copied at once)
+      int nb = 0, used = 0;
+      while (t < c1 && nb < kMaxBatch) {
+        int64_t gb;
+        int n, depth0, cell;
+        unit_at(P, U, t, gb, n, depth0, cell);
+        if (U.mode != 2 && (n <= P.n_min || n == 1)) {
+          // Sec. 3 "Input": cells with at most N_min particles are not merged
+          for (int i = tt; i < n; i += kThreads) {
+            const int src = orig_index(perm, gb, i);
+            P.perm_final[gb + i] = src;
+            P.head[gb + i] = kHeadSingle;
+            if (!PMA_SORTED_COPY) {  // (the sorted copy already sits there)
 #pragma unroll
-            for (int l = 0; l < D; ++l)
-              static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
-            static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+              for (int l = 0; l < D; ++l)
+                static_cast<T *>(P.fin[l])[gb + i] = StoreOf<T>::load(P.q[l], src);
+              static_cast<T *>(P.fin[D])[gb + i] = StoreOf<T>::load(P.w, src);
+            }
           }
+          passed += 1;
+          ++t;
+          continue;
         }
-        passed += 1;
-        continue;
+        if (n > cap) {
+          if (tt == 0) set_error(P.err, kErrInternal);
+          ++t;
+          continue;
+        }
+        if (used + n > cap) break;  // the next batch starts here
+        if (tt == 0) {
+          S.ev[kEvOff + nb] = used;
+          S.ev[kEvN + nb] = n;
+          S.ev[kEvGb + nb] = (int)gb;
+          S.ev[kEvCell + nb] = cell;
+          cnt.depth += (unsigned long long)depth0 * n;
+        }
+        if (U.mode != 2) merged += 1;
+        used += n;
+        ++nb;
+        ++t;
       }
-      if (n > cap) {
-        if (tt == 0) set_error(P.err, kErrInternal);
-        continue;
-      }
-      if (U.mode != 2) merged += 1;
-      if (tt == 0) cnt.depth += (unsigned long long)depth0 * n;
-      if (t + 1 < c1 && (!perm || PMA_SORTED_COPY) && tt < D + 1) {
+      if (nb == 0) continue;  // only pass-through cells were left
+      if (tt == 0) S.ev[kEvBatchN] = nb;
+      if (t < c1 && (!perm || PMA_SORTED_COPY) && tt < D + 1) {
         // the next unit of this chunk: pull its columns into L2 meanwhile
-        int64_t nb;
+        int64_t nbg;
         int nn, nd, nc;
-        unit_at(P, U, t + 1, nb, nn, nd, nc);
-        const int64_t ne = nb + nn;
+        unit_at(P, U, t, nbg, nn, nd, nc);
+        const int64_t ne = nbg + nn;
         const size_t es = sizeof(T);
         const char *col = static_cast<const char *>(
             PMA_SORTED_COPY ? P.fin[tt] : (tt < D ? P.q[tt] : P.w));
         // the 16-byte-aligned part of the range only: never outside the array
-        const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nb * es) + 15) & ~uintptr_t(15);
+        const uintptr_t a0 = (reinterpret_cast<uintptr_t>(col + nbg * es) + 15) & ~uintptr_t(15);
         const uintptr_t a1 = (reinterpret_cast<uintptr_t>(col + ne * es)) & ~uintptr_t(15);
         if (a1 > a0)
           asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0),
                        "r"((unsigned)(a1 - a0))
                        : "memory");
       }
+      __syncthreads();  // the batch table
       bool bad = false;
-      if (PMA_SORTED_COPY) {
+      for (int u = 0; u < nb; ++u) {
+        const int64_t gb = S.ev[kEvGb + u];
+        const int n = S.ev[kEvN + u], off = S.ev[kEvOff + u];
+        if (PMA_SORTED_COPY) {
 #pragma unroll 4
-        for (int i = tt; i < n; i += kThreads) {
+          for (int i = tt; i < n; i += kThreads) {
 #pragma unroll
-          for (int l = 0; l <= D; ++l) {
-            const T x = static_cast<const T *>(P.fin[l])[gb + i];
-            bad |= l < D ? !finite_val(x) : (!(x > T(0)) || !finite_val(x));
-            S.col(l)[i] = x;
+            for (int l = 0; l <= D; ++l) {
+              const T x = static_cast<const T *>(P.fin[l])[gb + i];
+              bad |= l < D ? !finite_val(x) : (!(x > T(0)) || !finite_val(x));
+              S.col(l)[off + i] = x;
+            }
+            S.idx(0)[off + i] = (uint16_t)(off + i);
           }
-          S.idx(0)[i] = (uint16_t)i;
-        }
-      } else {
+        } else {
 #pragma unroll 4
-        for (int i = tt; i < n; i += kThreads) {
-          const int src = orig_index(perm, gb, i);
+          for (int i = tt; i < n; i += kThreads) {
+            const int src = orig_index(perm, gb, i);
 #pragma unroll
-          for (int l = 0; l < D; ++l) {
-            const T x = StoreOf<T>::load(P.q[l], src);
-            bad |= !finite_val(x);
-            S.col(l)[i] = x;
+            for (int l = 0; l < D; ++l) {
+              const T x = StoreOf<T>::load(P.q[l], src);
+              bad |= !finite_val(x);
+              S.col(l)[off + i] = x;
+            }
+            const T w = StoreOf<T>::load(P.w, src);
+            bad |= !(w > T(0)) || !finite_val(w);
+            S.col(D)[off + i] = w;
+            S.idx(0)[off + i] = (uint16_t)(off + i);
           }
-          const T w = StoreOf<T>::load(P.w, src);
-          bad |= !(w > T(0)) || !finite_val(w);
-          S.col(D)[i] = w;
-          S.idx(0)[i] = (uint16_t)i;
         }
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) set_error(P.err, kErrInput);
       if (tt < kClasses) S.top[tt] = 0;
       __syncthreads();
       if (tt == 0) {
-        if (n == 1) {
-          // a one-particle piece is final at once
-          emit_single<T, D>(P, S, perm, gb, 0, 0);
-          cnt.leaves += 1;
-        } else {
-          const int c = size_class(n, S.base);
-          *S.rec(c, 0) = pack_rec(0, n, 0);
-          S.top[c] = 1;
+        for (int u = 0; u < nb; ++u) {
+          const int n = S.ev[kEvN + u], off = S.ev[kEvOff + u];
+          if (n == 1) {
+            // a one-particle piece is final at once
+            emit_single<T, D>(P, S, perm, 0, off, off);
+            cnt.leaves += 1;
+          } else {
+            // the units are disjoint subsets of the tile: within every
+            // class's capacity together
+            const int c = size_class(n, S.base);
+            *S.rec(c, S.top[c]) = pack_rec(off, n, 0);
+            S.top[c] += 1;
+          }
         }
       }
       // rounds: the team pops up to TEAM * 32/G subsets of the largest
@@ -905,7 +956,7 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           __syncthreads();
           if (tt == 0) S.top[c] = 0;
           __syncthreads();
-          if (wide_round<T, D, VAR, TEAM>(P, S, perm, gb, lane, wt, sub, W, act, rec, cnt))
+          if (wide_round<T, D, VAR, TEAM>(P, S, perm, 0, lane, wt, sub, W, act, rec, cnt))
             exact_sets<T, D, VAR>(P, S, 1u, rec, lane, cnt);
           continue;
         }
@@ -930,37 +981,44 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
         if (kw > 0) {
           unsigned pend;
           if (c == 0)
-            pend = pair_round<T, D, VAR>(P, S, perm, gb, lane, cnt, kw, rec);
+            pend = pair_round<T, D, VAR>(P, S, perm, 0, lane, cnt, kw, rec);
           else
-            pend = group_round<T, D, VAR, TEAM>(P, S, perm, gb, lg, lane, cnt, kw, rec);
+            pend = group_round<T, D, VAR, TEAM>(P, S, perm, 0, lg, lane, cnt, kw, rec);
           // FP32 storage: the rare FP64 rechecks, by the whole warp, after
           // its share of the round
           if (sizeof(T) == 4 && pend) exact_sets<T, D, VAR>(P, S, pend, rec, lane, cnt);
         }
         __syncwarp();
       }
-      // the unit in final order: permutation, head bytes, staged particles
-      for (int i = tt; i < n; i += kThreads) {
-        const int j = S.idx(0)[i];
-        if (j >= n) {
-          // only after an internal failure left a position unmarked
-          set_error(P.err, kErrInternal);
-          P.perm_final[gb + i] = -1;
-          P.head[gb + i] = 0;
-          continue;
+      // each unit in final order: permutation, head bytes, staged particles
+      for (int u = 0; u < nb; ++u) {
+        const int64_t gb = S.ev[kEvGb + u];
+        const int n = S.ev[kEvN + u], off = S.ev[kEvOff + u];
+        for (int i = tt; i < n; i += kThreads) {
+          const int j = S.idx(0)[off + i];
+          if (j < off || j >= off + n) {
+            // only after an internal failure left a position unmarked
+            set_error(P.err, kErrInternal);
+            P.perm_final[gb + i] = -1;
+            P.head[gb + i] = 0;
+            continue;
+          }
+          if (!check_index(P.check, P.err, gb + i < P.n, kChkStage, gb + i)) continue;
+          P.perm_final[gb + i] = orig_index(perm, gb, j - off);
+          P.head[gb + i] = (uint8_t)S.idx(1)[off + i];
+          stage<T, D>(P, S, gb + i, j);
         }
-        if (!check_index(P.check, P.err, gb + i < P.n, kChkStage, gb + i)) continue;
-        P.perm_final[gb + i] = orig_index(perm, gb, j);
-        P.head[gb + i] = (uint8_t)S.idx(1)[i];
-        stage<T, D>(P, S, gb + i, j);
       }
       __syncthreads();
-      if (tt == 0 && S.ev[0] != 0) {
-        // the unit's near-tie bits, into its cell's word
-        const unsigned f = (unsigned)S.ev[0];
-        S.ev[0] = 0;
-        if (atomicOr(&P.cell_flags[cell], f) == 0u)
-          atomicAdd(&P.stats[kStCellsFlagged], 1ull);
+      if (tt == 0) {
+        // each unit's near-tie bits, into its cell's word
+        for (int u = 0; u < nb; ++u) {
+          const unsigned f = (unsigned)S.ev[kEvBits + u];
+          if (f == 0u) continue;
+          S.ev[kEvBits + u] = 0;
+          if (atomicOr(&P.cell_flags[S.ev[kEvCell + u]], f) == 0u)
+            atomicAdd(&P.stats[kStCellsFlagged], 1ull);
+        }
       }
     }
   }
