@@ -74,6 +74,10 @@ def workload(name):
         return synth.shower()
     if name == "hot_6d":
         return synth.hot_6d()
+    if name == "hot_6d_small":
+        # 48^3 cells (about 1.3e7 particles, 350 MB in float32): the 6D
+        # hot-spot shape at a size for profiling captures
+        return synth.hot_6d(grid=(48, 48, 48))
     if name == "counter_beams":
         return synth.counter_beams()
     raise SystemExit("unknown workload " + name)

@@ -78,6 +78,7 @@ struct pma_handle {
   int mixed = 0;
   int cap = 0;
   int unit_grid = 0;
+  int unit_team = 8;               // warps of the large-cell and piece teams
   int cap_w = 0;
   int cap_t = 0;
   int class_base = kClassBaseMin;  // size classes of pending subsets
@@ -287,8 +288,13 @@ void apply_classes(pma_handle *h, const Classes &c) {
   h->tiny_grid = h->sms * std::min<int>(24, std::max<int>(1, (int)(smem_sm / (team_smem(
                                                                      h->mixed, h->D, c.cap_t) +
                                                                  1024))));
+  // large cells and pieces: 8-warp teams, or 12-warp teams when only one
+  // 8-warp CTA fits an SM (registers or shared memory): more warps to hide
+  // latency, where two 8-warp CTAs would give more if they fitted
+  const int b8 = team_blocks(h->mixed, h->D, 8, c.cap, h->smem_optin);
+  h->unit_team = b8 == 1 ? 12 : 8;
   h->unit_grid =
-      h->sms * std::max<int>(1, (int)(smem_sm / (team_smem(h->mixed, h->D, c.cap) + 1024)));
+      h->sms * (b8 == 1 ? team_blocks(h->mixed, h->D, 12, c.cap, h->smem_optin) : b8);
 }
 
 // the candidates the tuner times: tiny-class limit x small-class tile x
@@ -600,10 +606,12 @@ static int enqueue(pma_handle *h, int64_t n, const int32_t *cells, const void *c
   e = launch_team(P, h->mixed, 0, 4, h->cap_w, grid_for(pv.cells_small == 0, h->warp_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (small cells)");
   mark(h, 3, st);
-  e = launch_team(P, h->mixed, 1, 8, h->cap, grid_for(pv.cells_large == 0, h->unit_grid), st);
+  e = launch_team(P, h->mixed, 1, h->unit_team, h->cap,
+                  grid_for(pv.cells_large == 0, h->unit_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (large cells)");
   mark(h, 4, st);
-  e = launch_team(P, h->mixed, 2, 8, h->cap, grid_for(pv.big_cells == 0, h->unit_grid), st);
+  e = launch_team(P, h->mixed, 2, h->unit_team, h->cap,
+                  grid_for(pv.big_cells == 0, h->unit_grid), st);
   if (e != cudaSuccess) return cuda_fail(h, e, "team launch (pieces)");
   mark(h, 5, st);
 

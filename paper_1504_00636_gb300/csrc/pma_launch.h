@@ -21,6 +21,8 @@ cudaError_t launch_big(const Problem &P, int mixed, int grid, cudaStream_t st);
 // warp.cu: a team of `team` (4 or 8) warps per unit of up to `cap` particles;
 // mode 0 small-class cells, 1 large-class cells, 2 pieces of big cells
 size_t team_smem(int mixed, int D, int cap);
+// CTAs per SM of the large-cell team kernel (8 or 12 warps) at tile size cap
+int team_blocks(int mixed, int D, int team, int cap, int smem_optin);
 cudaError_t launch_team(const Problem &P, int mixed, int mode, int team, int cap, int grid,
                         cudaStream_t st);
 

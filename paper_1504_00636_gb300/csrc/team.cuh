@@ -2,8 +2,10 @@
 // memory (a cell, or a piece of a cell first cut in global memory), and the
 // verbatim copy of cells with N <= N_min.
 //
-// A team of 4 or 8 warps owns one unit at a time.  The unit's coordinates and
-// weights are staged once in shared memory (SoA columns) and stay in place.
+// A team of 1, 4, 8 or 12 warps owns one batch of units at a time: the
+// consecutive units of its ticket chunk that fit its tile together, side by
+// side.  Their coordinates and weights are staged once in shared memory (SoA
+// columns) and stay in place.
 // A subset is a contiguous range of a 16-bit index array; a cut writes
 // V1 = {q_k <= Q_k} to the front and V2 to the back of the same range in the
 // other index array (double-buffered by tree depth), so the final sets come
@@ -34,7 +36,7 @@ namespace pma {
 constexpr int kWarpChunk = 4;  // cells taken per work-counter increment
 constexpr int kClasses = 7;    // pairs, then G = 1, 2, 4, 8, 16, 32
 constexpr int kMaxCapW = 8191;
-constexpr int kMaxTeam = 8;    // warps of the largest team
+constexpr int kMaxTeam = 12;   // warps of the largest team
 
 // size class of a subset of m >= 2 particles for class base B: pairs, then
 // up to B, 2B, 4B, 8B, 16B particles, and more
@@ -385,7 +387,7 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
   Moments<T, D> M;
   M.zero();
   int run = (m + G - 1) >> lg;
-  if (TEAM == kMaxTeam && kF && G == 32 && m > kRunBlock * 32) {
+  if (TEAM >= 8 && kF && G == 32 && m > kRunBlock * 32) {
     // sets above 1024 particles (large tiles only): FP32 runs of at most
     // kRunBlock terms, each folded exactly into the compensated sums
     accumulate_blocked<T, D>(M, S, ix, b, m, gl, G, s);
@@ -487,7 +489,8 @@ __device__ unsigned group_round(const Problem &P, const WarpTile<T, D> &S, const
 }
 
 // A wide round: the (up to TEAM/2) pending sets of the largest class,
-// when they would leave warps idle, each get W = TEAM/2^k warps.
+// when they would leave warps idle, each get W warps: TEAM halved (rounded
+// down) until the sets fit the team (12, 6, 3, 1 for a 12-warp team).
 // Moments: each warp sums a strided share, the W partial sums are merged in
 // warp order through shared memory.  Cut: warp u of the group takes the
 // u-th contiguous segment of the set (32 lanes at a time, conflict-free), a
@@ -943,9 +946,9 @@ __global__ void __launch_bounds__(32 * TEAM, (team_min_blocks<T, D, TEAM>()))
           if (c < 0 && S.top[k] > 0) c = k;
         if (c < 0) break;
         const int avail = S.top[c];
-        if (TEAM == kMaxTeam && c == kClasses - 1 && avail * 2 <= TEAM) {
+        if (TEAM >= 8 && c == kClasses - 1 && avail * 2 <= TEAM) {
           // few large sets: several warps per set (wide round).  Only the
-          // 8-warp teams (one or two CTAs per SM) use it: in the 4-warp teams
+          // 8- and 12-warp teams (one or two CTAs per SM) use it: in the 4-warp teams
           // other CTAs fill the idle warps' issue slots, and the extra
           // barriers measured slower.
           int W = TEAM;
@@ -1080,6 +1083,34 @@ static cudaError_t launch_team_t(const Problem &P, const UnitSource &U, int cap,
   return cudaGetLastError();
 }
 
+// CTAs of one team kernel instance resident per SM at tile size cap (its
+// registers and shared memory), from the CUDA occupancy calculator; 1 when
+// it cannot tell.  The shared-memory limit is first raised to the opt-in
+// maximum (the launches only ever raise it further for their own tiles).
+template <typename T, int D, int TEAM>
+static int team_blocks_t(int cap, int smem_optin) {
+  const size_t smem = warp_region_bytes<T, D>(cap);
+  if (cudaFuncSetAttribute(team_kernel<T, D, TEAM, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin) != cudaSuccess)
+    return 1;
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, team_kernel<T, D, TEAM, false>, 32 * TEAM,
+                                                    smem) != cudaSuccess)
+    return 1;
+  return b < 1 ? 1 : b;
+}
+
+template <typename T, int TEAM>
+static int team_blocks_d(int D, int cap, int smem_optin) {
+  switch (D) {
+    case 2: return team_blocks_t<T, 2, TEAM>(cap, smem_optin);
+    case 3: return team_blocks_t<T, 3, TEAM>(cap, smem_optin);
+    case 4: return team_blocks_t<T, 4, TEAM>(cap, smem_optin);
+    case 5: return team_blocks_t<T, 5, TEAM>(cap, smem_optin);
+    default: return team_blocks_t<T, 6, TEAM>(cap, smem_optin);
+  }
+}
+
 template <typename T, int TEAM, bool VAR>
 static cudaError_t launch_team_d(const Problem &P, const UnitSource &U, int cap, int grid,
                                  cudaStream_t st) {
@@ -1102,6 +1133,13 @@ static cudaError_t launch_team_build(const Problem &P, const UnitSource &U, int 
   if (team == 4)
     return mixed ? launch_team_d<float, 4, VAR>(P, U, cap, grid, st)
                  : launch_team_d<double, 4, VAR>(P, U, cap, grid, st);
+  // 12-warp teams in the paper's-rule build only (the variant build keeps
+  // 8-warp teams for large cells: fewer instances to compile)
+  if constexpr (!VAR) {
+    if (team == 12)
+      return mixed ? launch_team_d<float, 12, VAR>(P, U, cap, grid, st)
+                   : launch_team_d<double, 12, VAR>(P, U, cap, grid, st);
+  }
   return mixed ? launch_team_d<float, 8, VAR>(P, U, cap, grid, st)
                : launch_team_d<double, 8, VAR>(P, U, cap, grid, st);
 }

@@ -10,6 +10,16 @@ size_t team_smem(int mixed, int D, int cap) {
 }
 
 // mode: 0 small-class cells, 1 large-class cells, 2 pieces of big cells
+int team_blocks(int mixed, int D, int team, int cap, int smem_optin) {
+  if (team == 12)
+    return mixed ? team_blocks_d<float, 12>(D, cap, smem_optin)
+                 : team_blocks_d<double, 12>(D, cap, smem_optin);
+  if (team == 8)
+    return mixed ? team_blocks_d<float, 8>(D, cap, smem_optin)
+                 : team_blocks_d<double, 8>(D, cap, smem_optin);
+  return 1;
+}
+
 cudaError_t launch_team(const Problem &P, int mixed, int mode, int team, int cap, int grid,
                         cudaStream_t st) {
   UnitSource U;
