@@ -78,36 +78,74 @@ __device__ __forceinline__ int chunk_slots(unsigned hw, int upto) {
   return v;
 }
 
+// The count kernel takes kCountTiles tiles per CTA and 16 consecutive head
+// bytes per thread (one 16-byte load), so that each thread has a useful
+// amount of memory in flight: a tile is the 64 threads of two warps.
+constexpr int kCountTiles = 4;
+constexpr int kCountPer = 16;
+static_assert(kEmitTile / kCountPer == 64 && kEmitThreads == 64 * kCountTiles,
+              "a tile is two warps of the count kernel");
+
+// output slots of the 16 positions c0 .. c0 + 15 (c0 a multiple of 16; the
+// head array is padded to a multiple of 16 bytes, and bytes at n and beyond
+// are never counted)
+template <bool EC>
+__device__ __forceinline__ int slots16(const uint8_t *head, int64_t c0, int64_t n) {
+  if (c0 + kCountPer <= n) {
+    const uint4 q = *reinterpret_cast<const uint4 *>(head + c0);
+    return chunk_slots<EC>(q.x, kEmitChunk) + chunk_slots<EC>(q.y, kEmitChunk) +
+           chunk_slots<EC>(q.z, kEmitChunk) + chunk_slots<EC>(q.w, kEmitChunk);
+  }
+  int v = 0;
+#pragma unroll
+  for (int k = 0; k < kCountPer / kEmitChunk; ++k)
+    v += chunk_slots<EC>(load_heads(head, c0 + k * kEmitChunk, n), kEmitChunk);
+  return v;
+}
+
 template <bool EC>
 __global__ void __launch_bounds__(kEmitThreads) count_kernel(EmitArgs a) {
-  __shared__ int s_warp[32];
+  __shared__ int s_warp[kEmitThreads / 32];
   if (timed_out(a.err)) return;
-  const int64_t c0 = (int64_t)blockIdx.x * kEmitTile + (int64_t)threadIdx.x * kEmitChunk;
-  int v = chunk_slots<EC>(load_heads(a.head, c0, a.n), kEmitChunk);
+  const int64_t c0 = (int64_t)blockIdx.x * (kEmitTile * kCountTiles) +
+                     (int64_t)threadIdx.x * kCountPer;
+  int v = slots16<EC>(a.head, c0, a.n);
 #pragma unroll
   for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
   if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int k = 0; k < kEmitThreads / 32; ++k) t += s_warp[k];
-    a.tile_count[blockIdx.x] = t;
+  if (threadIdx.x < kCountTiles) {
+    const int t = blockIdx.x * kCountTiles + threadIdx.x;
+    if (t < a.tiles) a.tile_count[t] = s_warp[2 * threadIdx.x] + s_warp[2 * threadIdx.x + 1];
   }
 }
 
-// one CTA: exclusive prefix of the tile counts, and the total M
+// one CTA: exclusive prefix of the tile counts (four consecutive tiles per
+// thread), and the total M
+constexpr int kScanPer = 4;
 __global__ void __launch_bounds__(kScanCta) tiles_kernel(EmitArgs a) {
   __shared__ int s_warp[32];
   __shared__ long long s_carry;
   if (timed_out(a.err)) return;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (int base = 0; base < a.tiles; base += kScanCta) {
-    const int i = base + threadIdx.x;
-    const int v = i < a.tiles ? a.tile_count[i] : 0;
+  for (int base = 0; base < a.tiles; base += kScanCta * kScanPer) {
+    const int i0 = base + threadIdx.x * kScanPer;
+    int v[kScanPer];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      v[k] = i0 + k < a.tiles ? a.tile_count[i0 + k] : 0;
+      sum += v[k];
+    }
     int total;
-    const int ex = block_exclusive_scan(v, s_warp, &total);
-    if (i < a.tiles) a.tile_prefix[i] = s_carry + ex;
+    const int ex = block_exclusive_scan(sum, s_warp, &total);
+    long long run = s_carry + ex;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      if (i0 + k < a.tiles) a.tile_prefix[i0 + k] = run;
+      run += v[k];
+    }
     __syncthreads();
     if (threadIdx.x == 0) s_carry += total;
     __syncthreads();
@@ -729,10 +767,11 @@ static cudaError_t launch_emit_t(const EmitArgs &a, cudaStream_t st) {
 
 cudaError_t launch_emit(const EmitArgs &a, cudaStream_t st) {
   if (a.tiles <= 0) return cudaSuccess;
+  const int count_grid = (a.tiles + kCountTiles - 1) / kCountTiles;
   if (a.ec)
-    count_kernel<true><<<a.tiles, kEmitThreads, 0, st>>>(a);
+    count_kernel<true><<<count_grid, kEmitThreads, 0, st>>>(a);
   else
-    count_kernel<false><<<a.tiles, kEmitThreads, 0, st>>>(a);
+    count_kernel<false><<<count_grid, kEmitThreads, 0, st>>>(a);
   tiles_kernel<<<1, kScanCta, 0, st>>>(a);
   // the energy sums are a separate build: they cost the plain path registers
   const bool en = a.energy != nullptr;

@@ -306,6 +306,30 @@ def test_mixed_rechecks_close_decisions_in_fp64():
 
 # --------------------------------------------------------- API behaviour
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shorter_call_ignores_the_longer_calls_head_bytes(precision):
+    # the same handle merges 96 two-stream cells, then the first 41 cells
+    # minus 7 particles (a length that is not a multiple of 16): Step 7 must
+    # count only the positions of the second call, although the workspace
+    # still holds the first call's head bytes after them
+    p = synth.two_stream(cells=96)
+    if precision == "mixed":
+        p = p.astype(np.float32)
+    m = binding.Merger(p.dx, p.dp, p.n_cells, p.n, p.cell_size, 0, precision)
+    run_gpu(p, precision, merger=m)
+    n2 = int(np.searchsorted(p.cell, 41)) - 7
+    q = dataclasses.replace(p, cell=p.cell[:n2].copy(), pos=p.pos[:, :n2].copy(),
+                            mom=p.mom[:, :n2].copy(), w=p.w[:n2].copy())
+    assert n2 % 16 != 0
+    g = run_gpu(q, precision, merger=m)
+    m.close()
+    r = _oracle(q)
+    rep = compare(q, g, r, mixed=precision == "mixed")
+    assert rep["unexplained"] == 0
+    assert g["count_dev"] == g["count"]
+    conservation(q, g)
+
+
 def test_async_merge_then_sync_and_host_variant():
     import torch
     p = synth.two_stream(cells=16)
