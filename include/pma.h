@@ -270,7 +270,8 @@ int pma_test_status_of_bits(unsigned bits);
  *   caps[0] = cap_t  cells of at most cap_t particles: one-warp teams
  *   caps[1] = cap_w  up to cap_w: 4-warp teams (cap_w <= 1024)
  *   caps[2] = cap    up to cap: 8-warp teams with a tile of cap particles
- *                    (cap <= 8191 and what one CTA's shared memory holds);
+ *                    (cap <= 8191 and what one CTA's shared memory holds;
+ *                    12-warp teams where only one 8-warp CTA fits an SM);
  *                    larger cells are first cut in global memory and their
  *                    pieces join this class
  *   caps[3] = base   the class base B, 12 <= B <= 32: subsets of 3 to B

@@ -256,7 +256,7 @@ def pma_probe_fma(precision: str):
 
 def pma_get_classes(handle):
     """(cap_t, cap_w, cap, base, widen): the population limits of the
-    one-warp, 4-warp and 8-warp team paths, the class base of the subset size
+    one-warp, 4-warp and 8-warp (or 12-warp) team paths, the class base of the subset size
     classes, and whether sparse rounds widen the lane groups."""
     c = (ctypes.c_int32 * 5)()
     _check(load().pma_get_classes(handle, c), handle)
