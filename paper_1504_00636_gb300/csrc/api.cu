@@ -23,6 +23,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lookback.cuh"
 #include "pma.h"
 #include "pma_launch.h"
@@ -110,6 +112,7 @@ struct pma_handle {
   Staging stage;
   bool timing = false;
   int timed = 0;     // calls recorded since timing was enabled
+  int nvtx_depth = 0;  // NVTX ranges of the current call still open
   unsigned long long wait_ns = 0;  // limit of the bounded device waits (0: default)
   int withhold_tile = -1;          // failure-detection test hook (see pma.h)
   cudaEvent_t ev[kRing][PMA_N_STAGES] = {};  // PMA_N_STAGES events per call
@@ -167,10 +170,32 @@ void free_all(pma_handle *h) {
       if (e) cudaEventDestroy(e);
 }
 
+// NVTX ranges of a call and of its stages, for profilers that show host
+// ranges beside the kernels (no-ops unless a profiler is attached)
+const char *const kStageRange[PMA_N_STAGES - 1] = {
+    "pma Step 1 binning", "pma big-cell cuts", "pma small-cell teams",
+    "pma large-cell teams", "pma big-cell pieces", "pma Step 7 emit"};
+
 // event i of the current call: 0 before binning, 1..6 after each stage
-// (stage k spans events k..k+1, the whole call 0..6)
+// (stage k spans events k..k+1, the whole call 0..6); the NVTX range of the
+// call opens at 0 and closes at 6, one stage range at a time in between
 void mark(pma_handle *h, int i, cudaStream_t st) {
   if (h->timing && h->cur_ev) cudaEventRecord(h->cur_ev[i], st);
+  if (i == 0) {
+    // ranges that an earlier call left open when it returned an error
+    for (; h->nvtx_depth > 0; --h->nvtx_depth) nvtxRangePop();
+    nvtxRangePushA("pma_merge");
+    nvtxRangePushA(kStageRange[0]);
+    h->nvtx_depth = 2;
+  } else if (h->nvtx_depth == 2) {
+    nvtxRangePop();
+    if (i < PMA_N_STAGES - 1) {
+      nvtxRangePushA(kStageRange[i]);
+    } else {
+      nvtxRangePop();
+      h->nvtx_depth = 0;
+    }
+  }
 }
 
 // status code of a device error word: bad particle data first, then a wait
